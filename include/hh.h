@@ -1,0 +1,159 @@
+/*
+ * hh.h -- C ABI of libhh, GB300 (sm_103a) kernels for products of Householder
+ * reflectors, after Rusu, "Approximate Eigenvalue Decompositions of Linear
+ * Transformations with a Few Householder Reflectors" (arXiv 1811.07624).
+ *
+ * The transform.  A plan holds h reflector vectors v_1..v_h of length n.
+ * Reflector k is H_k = I - 2 u_k u_k^T with u_k = v_k / |v_k| (§II-A, Eq. (2));
+ * a zero v_k means H_k = I (the "u_k = 0" reflector of Result 1, §II-B).  The
+ * chain is W = H_1 H_2 ... H_h, so H_h acts first in W x.  The plan may carry
+ * a +-1 sign vector sigma (the diagonal D of Eq. (1)) and a spectrum d (the
+ * s-bar of Eq. (21)).  Per row x of X the library computes
+ *
+ *   hh_apply      y = sigma .* (W x)                       (Eq. (1))
+ *   hh_apply_T    y = W^T (sigma .* x)                     (right factor of Eq. (21))
+ *   hh_apply_sym  y = sigma .* W (d .* W^T (sigma .* x))   (Eq. (21))
+ *
+ * and the gradients of a scalar loss through each of them (hh_backward), and
+ * the fast Mahalanobis distance of §IV-C (hh_mahalanobis).  The paper counts
+ * 4nh operations per W x (§II-A) and (8h+1)n per S x (§III-A).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named X, Y, U, d, sign, gX, gY, gU, gd, ia, ib, out are DEVICE
+ *    pointers (memory of the current CUDA device).  Host pointers are rejected
+ *    with HH_ERR_INVALID_ARG where the runtime can tell them apart.  There is
+ *    no CPU fallback: every step runs in this library's CUDA kernels.
+ *  - Vectors are rows: X is batch x n, row b at X + b*ldx elements, ldx >= n.
+ *    Reflectors are rows too: v_k at U + k*ldu elements, ldu >= n.
+ *  - Element type is the plan's dtype: HH_F32 (float), HH_F64 (double) or
+ *    HH_BF16 (bfloat16 storage of U, X and Y; FP32 accumulation; the
+ *    normalisation and the compact-WY T factor are kept in FP64).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Apply, backward and distance calls are asynchronous on it:
+ *    argument errors are reported synchronously, kernel results are ready
+ *    when the stream is.  hh_create and hh_destroy synchronise `stream`.
+ *  - In-place (Y == X, same ld) is allowed for the three apply calls.
+ *    Other overlaps between inputs and outputs are undefined.
+ *  - A plan is read-only after hh_create, so one plan may be used from
+ *    several streams or host threads at once.
+ *  - The caller owns X, Y and every gradient and output buffer.  The plan
+ *    copies U, d and sign; the caller may free them once hh_create returns.
+ *  - On failure an entry point returns a non-zero hh_status, writes nothing it
+ *    was asked to write (argument errors) and records a message that
+ *    hh_last_error() returns on the same host thread.
+ */
+#ifndef HH_H_
+#define HH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HH_OK = 0,
+    HH_ERR_INVALID_ARG = 1, /* bad size, null or host pointer, misuse */
+    HH_ERR_UNSUPPORTED = 2, /* valid request this build has no kernel for */
+    HH_ERR_NONFINITE = 3,   /* U or d holds NaN/Inf (checked at create) */
+    HH_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    HH_ERR_OOM = 5,         /* device allocation failed */
+    HH_ERR_TIMEOUT = 6      /* a bounded device-side wait expired */
+} hh_status;
+
+typedef enum { HH_F32 = 0, HH_F64 = 1, HH_BF16 = 2 } hh_dtype;
+
+typedef enum { HH_MODE_W = 0, HH_MODE_WT = 1, HH_MODE_SYM = 2 } hh_mode;
+
+/* Kernel family for the apply calls.  FUSED: one pass, each vector read and
+ * written once, reflectors applied one after another on CUDA cores (F32, F64).
+ * WY: compact-WY regrouping W = I - V T V^T run as tcgen05 GEMMs (BF16).
+ * AUTO picks FUSED for F32/F64 and WY for BF16. */
+typedef enum { HH_PATH_AUTO = 0, HH_PATH_FUSED = 1, HH_PATH_WY = 2 } hh_path;
+
+typedef struct hh_plan_s *hh_plan_t;
+
+/*
+ * Create a plan for the h reflectors in U (device, dtype elements, reflector k
+ * at U + k*ldu) and the optional spectrum d (device, n elements of dtype, or
+ * NULL: then hh_apply_sym and hh_mahalanobis fail with HH_ERR_INVALID_ARG).
+ * Reflector vectors need not be unit length; they are normalised in FP64
+ * (tau_k = 2 / v_k^T v_k, §II-A Eq. (2)).  Requires n >= 1, h >= 0.
+ * The paper's regime is h < n/2 (§II-A); larger h is accepted.
+ * Returns HH_ERR_NONFINITE if U or d holds a NaN or Inf.
+ * Same as hh_create_ex(out, n, h, U, ldu, d, NULL, dtype, HH_PATH_AUTO, NULL).
+ */
+hh_status hh_create(hh_plan_t *out, int64_t n, int64_t h, const void *U, int64_t ldu,
+                    const void *d, hh_dtype dtype);
+
+/*
+ * hh_create with a sign vector and an explicit path.  sign: device int8
+ * vector of n entries, each +1 or -1, or NULL for all +1 (the diagonal D of
+ * Eq. (1)); any other value gives HH_ERR_INVALID_ARG.  The plan's device
+ * memory is allocated with cudaMalloc here and freed by hh_destroy.
+ */
+hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int64_t ldu,
+                       const void *d, const int8_t *sign, hh_dtype dtype, hh_path path,
+                       void *stream);
+
+/* Release a plan (NULL is a no-op).  Synchronises the device first. */
+hh_status hh_destroy(hh_plan_t plan);
+
+/* Shape and kernel family of a plan.  Any output pointer may be NULL. */
+hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype,
+                       hh_path *path);
+
+/*
+ * Y = sigma .* (W X) row by row (§II-A, Eq. (1)).  X: batch x n, row stride
+ * ldx; Y: batch x n, row stride ldy.  batch == 0 is a no-op.
+ */
+hh_status hh_apply(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                   int64_t batch, void *stream);
+
+/* Y = W^T (sigma .* X) row by row (the right-hand factor of Eq. (21)). */
+hh_status hh_apply_T(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                     int64_t batch, void *stream);
+
+/* Y = sigma .* W (d .* W^T (sigma .* X)) row by row (§III-A, Eq. (21)):
+ * the symmetric matrix D W diag(d) W^T D applied in one pass. */
+hh_status hh_apply_sym(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                       int64_t batch, void *stream);
+
+/*
+ * Gradients of a scalar loss L through hh_apply (mode HH_MODE_W), hh_apply_T
+ * (HH_MODE_WT) or hh_apply_sym (HH_MODE_SYM), given gY = dL/dY.
+ *   saved: the forward OUTPUT Y for modes W and WT (the intermediate vectors
+ *          are recomputed from it by the involution H_k H_k = I, §II-A, so
+ *          none are stored); the forward INPUT X for mode SYM.
+ *   gX:    dL/dX (batch x n, ldgx), or NULL to skip.
+ *   gU:    dL/dv_k for the reflector vectors as passed to hh_create (h rows of
+ *          n, row stride n), summed over the batch; or NULL to skip.
+ *   gd:    dL/dd (n), summed over the batch, mode SYM only; or NULL.
+ * F32 and F64 plans only.  Needs device scratch, allocated per call with
+ * cudaMallocAsync on `stream`.
+ */
+hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t lds,
+                      const void *gY, int64_t ldgy, void *gX, int64_t ldgx, void *gU,
+                      void *gd, int64_t batch, void *stream);
+
+/*
+ * Fast Mahalanobis distances (§IV-C): for p < npairs,
+ *   out[p] = (x_a - x_b)^T S (x_a - x_b) = sum_m d_m [W^T (sigma .* (x_a - x_b))]_m^2
+ * with x_a = row ia[p] and x_b = row ib[p] of X (int64 device indices, each
+ * in [0, nrows)).  out: npairs elements of the plan's dtype.  Needs d.
+ */
+hh_status hh_mahalanobis(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
+                         const int64_t *ia, const int64_t *ib, int64_t npairs, void *out,
+                         void *stream);
+
+/* Message for the last failed call on this host thread ("" if none). */
+const char *hh_last_error(void);
+
+/* Library version string. */
+const char *hh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HH_H_ */

@@ -1,0 +1,134 @@
+"""Python face of libhh: a plan object over torch CUDA tensors.
+
+The calls pass tensor pointers, leading dimensions and the current torch
+stream to the C ABI (``include/hh.h``); PyTorch only provides device memory
+and streams.  Transform (§II-A Eq. (1), §III-A Eq. (21)): W = H_1 ... H_h,
+H_k = I - 2 u_k u_k^T, u_k = v_k / |v_k|;
+
+    apply(X)      -> sigma .* (W x)                        per row x of X
+    apply_T(X)    -> W^T (sigma .* x)
+    apply_sym(X)  -> sigma .* W (d .* W^T (sigma .* x))
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+_TORCH_DTYPES = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16"}
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _rows(t: torch.Tensor, name: str, n: int, dtype: torch.dtype):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} has dtype {t.dtype}, the plan computes in {dtype}")
+    if t.dim() != 2 or t.shape[1] != n:
+        raise ValueError(f"{name} must have shape (batch, {n}), got {tuple(t.shape)}")
+    if t.shape[0] > 0 and t.stride(1) != 1:
+        raise ValueError(f"{name} rows must be contiguous (stride(1) == 1)")
+    ld = t.stride(0) if t.shape[0] > 1 else max(t.stride(0), n)
+    return t.data_ptr(), max(ld, n)
+
+
+class Plan:
+    """A created transform: h reflectors of length n, optional spectrum and sign.
+
+    U: CUDA tensor (h, n) of float32, float64 or bfloat16 (rows are v_k, any
+    non-zero norm; zero rows are identity factors).  d: optional (n,) spectrum.
+    sign: optional (n,) tensor of +-1 (converted to int8).  path: "auto",
+    "fused" or "wy".
+    """
+
+    def __init__(self, U: torch.Tensor, d: torch.Tensor | None = None,
+                 sign: torch.Tensor | None = None, path: str = "auto", stream=None):
+        if U.dim() != 2:
+            raise ValueError("U must be 2-D (h, n)")
+        if U.dtype not in _TORCH_DTYPES:
+            raise ValueError(f"unsupported dtype {U.dtype}")
+        if not U.is_cuda:
+            raise ValueError("U must be a CUDA tensor")
+        self.h, self.n = int(U.shape[0]), int(U.shape[1])
+        self.dtype = U.dtype
+        U = U.contiguous()
+        dd = None
+        if d is not None:
+            dd = d.to(device=U.device, dtype=U.dtype).contiguous()
+            if dd.shape != (self.n,):
+                raise ValueError("d must have shape (n,)")
+        ss = None
+        if sign is not None:
+            ss = sign.to(device=U.device, dtype=torch.int8).contiguous()
+            if ss.shape != (self.n,):
+                raise ValueError("sign must have shape (n,)")
+        self.has_d = dd is not None
+        self.device = U.device
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(U.device):
+            _lib.call("hh_create_ex", ctypes.byref(handle), self.n, self.h,
+                      U.data_ptr() if self.h > 0 else None, self.n,
+                      dd.data_ptr() if dd is not None else None,
+                      ss.data_ptr() if ss is not None else None,
+                      _lib.DTYPES[_TORCH_DTYPES[U.dtype]], _lib.PATHS[path],
+                      _stream_ptr(stream))
+        self._h = handle
+        n64, h64, dt, pa = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _lib.call("hh_plan_info", self._h, ctypes.byref(n64), ctypes.byref(h64),
+                  ctypes.byref(dt), ctypes.byref(pa))
+        self.path = {v: k for k, v in _lib.PATHS.items()}[pa.value]
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.call("hh_destroy", self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    # -- forward ------------------------------------------------------------------
+    def _apply(self, fn: str, X: torch.Tensor, out: torch.Tensor | None, stream) -> torch.Tensor:
+        xp, ldx = _rows(X, "X", self.n, self.dtype)
+        if out is None:
+            out = torch.empty((X.shape[0], self.n), device=X.device, dtype=self.dtype)
+        yp, ldy = _rows(out, "out", self.n, self.dtype)
+        if out.shape[0] != X.shape[0]:
+            raise ValueError("out must have as many rows as X")
+        _lib.call(fn, self._h, xp, ldx, yp, ldy, X.shape[0], _stream_ptr(stream))
+        return out
+
+    def apply(self, X, out=None, stream=None):
+        """sigma .* (W x) per row (Eq. (1))."""
+        return self._apply("hh_apply", X, out, stream)
+
+    def apply_T(self, X, out=None, stream=None):
+        """W^T (sigma .* x) per row."""
+        return self._apply("hh_apply_T", X, out, stream)
+
+    def apply_sym(self, X, out=None, stream=None):
+        """sigma .* W (d .* W^T (sigma .* x)) per row (Eq. (21))."""
+        return self._apply("hh_apply_sym", X, out, stream)
+
+    def apply_mode(self, mode: str, X, out=None, stream=None):
+        return {"W": self.apply, "WT": self.apply_T, "SYM": self.apply_sym}[mode](X, out, stream)

@@ -1,0 +1,241 @@
+// C ABI of libhh: argument checks, plan lifetime, dispatch to the kernels.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <new>
+
+#include "hh_internal.cuh"
+
+namespace hh {
+
+static thread_local std::string g_last_error;
+
+hh_status fail(hh_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+hh_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(HH_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(HH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// A pointer the current device's kernels may dereference: device memory of the
+// current device, or managed memory.  Host and unregistered pointers are not.
+static bool device_ptr(const void *p, int dev) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+static void free_plan(Plan *p) {
+    if (!p) return;
+    cudaFree(p->u);
+    cudaFree(p->d);
+    cudaFree(p->sign);
+    cudaFree(p->tau);
+    cudaFree(p->vnorm);
+    delete p;
+}
+
+static hh_status check_plan(const Plan *p) {
+    if (!p) return fail(HH_ERR_INVALID_ARG, "plan is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device)
+        return fail(HH_ERR_INVALID_ARG, "plan was created on device %d, current device is %d",
+                    p->device, dev);
+    return HH_OK;
+}
+
+static hh_status check_rows(const Plan *p, const void *A, int64_t lda, int64_t batch,
+                            const char *name) {
+    if (lda < p->n) return fail(HH_ERR_INVALID_ARG, "%s: leading dimension %lld < n = %lld", name,
+                                (long long)lda, (long long)p->n);
+    if (batch > 0 && !device_ptr(A, p->device))
+        return fail(HH_ERR_INVALID_ARG, "%s: not a device pointer of device %d", name, p->device);
+    return HH_OK;
+}
+
+static hh_status apply_common(hh_plan_t plan, hh_mode mode, const void *X, int64_t ldx, void *Y,
+                              int64_t ldy, int64_t batch, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st = check_plan(p);
+    if (st) return st;
+    if (batch < 0) return fail(HH_ERR_INVALID_ARG, "batch %lld < 0", (long long)batch);
+    if ((st = check_rows(p, X, ldx, batch, "X"))) return st;
+    if ((st = check_rows(p, Y, ldy, batch, "Y"))) return st;
+    if (mode == HH_MODE_SYM && !p->d)
+        return fail(HH_ERR_INVALID_ARG, "apply_sym: the plan has no spectrum d");
+    if (X == Y && ldx != ldy)
+        return fail(HH_ERR_INVALID_ARG, "in-place apply needs ldx == ldy");
+    if (batch == 0) return HH_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->path == HH_PATH_FUSED) return fused_apply(p, mode, X, ldx, Y, ldy, batch, s);
+    return fail(HH_ERR_UNSUPPORTED, "no kernel for this plan's path");
+}
+
+}  // namespace hh
+
+using namespace hh;
+
+extern "C" {
+
+const char *hh_last_error(void) { return g_last_error.c_str(); }
+
+const char *hh_version(void) { return "libhh 0.1 (sm_103a)"; }
+
+hh_status hh_create(hh_plan_t *out, int64_t n, int64_t h, const void *U, int64_t ldu,
+                    const void *d, hh_dtype dtype) {
+    return hh_create_ex(out, n, h, U, ldu, d, nullptr, dtype, HH_PATH_AUTO, nullptr);
+}
+
+hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int64_t ldu,
+                       const void *d, const int8_t *sign, hh_dtype dtype, hh_path path,
+                       void *stream) {
+    if (!out) return fail(HH_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1) return fail(HH_ERR_INVALID_ARG, "n = %lld < 1", (long long)n);
+    if (h < 0) return fail(HH_ERR_INVALID_ARG, "h = %lld < 0", (long long)h);
+    if (n > (int64_t(1) << 24) || h > (int64_t(1) << 20))
+        return fail(HH_ERR_INVALID_ARG, "n = %lld or h = %lld too large", (long long)n,
+                    (long long)h);
+    if (dtype != HH_F32 && dtype != HH_F64 && dtype != HH_BF16)
+        return fail(HH_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (path != HH_PATH_AUTO && path != HH_PATH_FUSED && path != HH_PATH_WY)
+        return fail(HH_ERR_INVALID_ARG, "unknown path %d", (int)path);
+    if (path == HH_PATH_AUTO) path = dtype == HH_BF16 ? HH_PATH_WY : HH_PATH_FUSED;
+    if (path == HH_PATH_FUSED && dtype == HH_BF16)
+        return fail(HH_ERR_UNSUPPORTED, "the fused path computes in F32 or F64");
+    if (path == HH_PATH_WY)
+        return fail(HH_ERR_UNSUPPORTED, "the compact-WY path is not built in this version");
+    if (h > 0 && ldu < n)
+        return fail(HH_ERR_INVALID_ARG, "ldu = %lld < n = %lld", (long long)ldu, (long long)n);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (h > 0 && !device_ptr(U, dev))
+        return fail(HH_ERR_INVALID_ARG, "U: not a device pointer of device %d", dev);
+    if (d && !device_ptr(d, dev))
+        return fail(HH_ERR_INVALID_ARG, "d: not a device pointer of device %d", dev);
+    if (sign && !device_ptr(sign, dev))
+        return fail(HH_ERR_INVALID_ARG, "sign: not a device pointer of device %d", dev);
+
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return fail(HH_ERR_OOM, "host allocation failed");
+    p->n = n;
+    p->h = h;
+    p->dtype = dtype;
+    p->path = path;
+    p->device = dev;
+    p->ldv = padded_ld(n);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int *flag = nullptr;
+    hh_status st = HH_OK;
+    size_t es = dtype_size(dtype);
+    if ((e = cudaMalloc(&p->u, es * (size_t)p->ldv * (size_t)(h > 0 ? h : 1))) ||
+        (e = cudaMalloc(&p->tau, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
+        (e = cudaMalloc(&p->vnorm, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
+        (d && (e = cudaMalloc(&p->d, es * (size_t)p->ldv))) ||
+        (sign && (e = cudaMalloc(&p->sign, es * (size_t)p->ldv))) ||
+        (e = cudaMalloc(&flag, sizeof(int)))) {
+        st = cuda_fail(e, "cudaMalloc (plan)");
+        goto done;
+    }
+    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s))) {
+        st = cuda_fail(e, "cudaMemsetAsync");
+        goto done;
+    }
+    st = prepare_fused(p, U, ldu, d, sign, flag, s);
+    if (st) goto done;
+    {
+        int hflag = 0;
+        if ((e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaStreamSynchronize(s))) {
+            st = cuda_fail(e, "plan preparation");
+            goto done;
+        }
+        if (hflag & 1) st = fail(HH_ERR_NONFINITE, "U holds a NaN or Inf");
+        else if (hflag & 2) st = fail(HH_ERR_NONFINITE, "d holds a NaN or Inf");
+        else if (hflag & 4) st = fail(HH_ERR_INVALID_ARG, "sign holds a value other than +1/-1");
+    }
+done:
+    cudaFree(flag);
+    if (st) {
+        free_plan(p);
+        return st;
+    }
+    *out = reinterpret_cast<hh_plan_t>(p);
+    return HH_OK;
+}
+
+hh_status hh_destroy(hh_plan_t plan) {
+    if (!plan) return HH_OK;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(p);
+    if (cur != p->device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize (destroy)");
+    return HH_OK;
+}
+
+hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype, hh_path *path) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p) return fail(HH_ERR_INVALID_ARG, "plan is NULL");
+    if (n) *n = p->n;
+    if (h) *h = p->h;
+    if (dtype) *dtype = p->dtype;
+    if (path) *path = p->path;
+    return HH_OK;
+}
+
+hh_status hh_apply(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                   int64_t batch, void *stream) {
+    return apply_common(plan, HH_MODE_W, X, ldx, Y, ldy, batch, stream);
+}
+
+hh_status hh_apply_T(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                     int64_t batch, void *stream) {
+    return apply_common(plan, HH_MODE_WT, X, ldx, Y, ldy, batch, stream);
+}
+
+hh_status hh_apply_sym(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                       int64_t batch, void *stream) {
+    return apply_common(plan, HH_MODE_SYM, X, ldx, Y, ldy, batch, stream);
+}
+
+hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t lds,
+                      const void *gY, int64_t ldgy, void *gX, int64_t ldgx, void *gU, void *gd,
+                      int64_t batch, void *stream) {
+    (void)plan; (void)mode; (void)saved; (void)lds; (void)gY; (void)ldgy; (void)gX; (void)ldgx;
+    (void)gU; (void)gd; (void)batch; (void)stream;
+    return fail(HH_ERR_UNSUPPORTED, "hh_backward is not built in this version");
+}
+
+hh_status hh_mahalanobis(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
+                         const int64_t *ia, const int64_t *ib, int64_t npairs, void *out,
+                         void *stream) {
+    (void)plan; (void)X; (void)ldx; (void)nrows; (void)ia; (void)ib; (void)npairs; (void)out;
+    (void)stream;
+    return fail(HH_ERR_UNSUPPORTED, "hh_mahalanobis is not built in this version");
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Internal declarations shared by the libhh translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hh.h"
+
+namespace hh {
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Row stride (elements) of every per-plan vector stored on the device: the
+// next power of two >= max(n, 1024) up to 16384, else n rounded up to 1024.
+// Every fused-kernel column tiling covers at most this many columns, so the
+// kernels read zero padding, never past the allocation.
+inline int64_t padded_ld(int64_t n) {
+    if (n <= 16384) {
+        int64_t c = 1024;
+        while (c < n) c *= 2;
+        return c;
+    }
+    return round_up(n, 1024);
+}
+
+struct Plan {
+    int64_t n = 0, h = 0;
+    hh_dtype dtype = HH_F32;
+    hh_path path = HH_PATH_FUSED;
+    int device = 0;
+    int64_t ldv = 0;        // padded row stride of every stored vector, elements
+    // FUSED path, compute dtype (float or double):
+    void *u = nullptr;      // h x ldv, u'_k = sqrt(tau_k) v_k, so H_k z = z - u'_k (u'_k . z)
+    void *d = nullptr;      // ldv, spectrum (zero padded), or null
+    void *sign = nullptr;   // ldv, +-1 (one padded), or null
+    double *tau = nullptr;  // h, tau_k = 2 / v_k^T v_k (0 for v_k = 0)
+    double *vnorm = nullptr;// h, |v_k|
+    // WY path (BF16 storage): filled by wy_prepare
+    void *wy = nullptr;
+};
+
+// Thread-local error message, set by fail().
+hh_status fail(hh_status st, const char *fmt, ...);
+hh_status cuda_fail(cudaError_t e, const char *what);
+
+inline size_t dtype_size(hh_dtype t) {
+    return t == HH_F64 ? 8 : (t == HH_BF16 ? 2 : 4);
+}
+
+// ---- prepare (hh_prepare.cu) ----
+// Normalise the reflectors in FP64 and write the plan's device vectors.
+// Sets *nonfinite (device int) if U or d holds a NaN/Inf.
+hh_status prepare_fused(Plan *p, const void *U, int64_t ldu, const void *d, const int8_t *sign,
+                        int *bad_flag, cudaStream_t st);
+
+// ---- fused apply (hh_fused.cu) ----
+hh_status fused_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void *Y,
+                      int64_t ldy, int64_t batch, cudaStream_t st);
+
+}  // namespace hh

@@ -1,0 +1,102 @@
+// Plan preparation (create time, not on the hot path): reflector normalisation
+// in FP64 and the padded device copies of the reflectors, spectrum and sign.
+//
+// Reflector k is H_k = I - tau_k v_k v_k^T with tau_k = 2 / (v_k^T v_k)
+// (§II-A, Eq. (2) with u_k = v_k / |v_k|); tau_k = 0 when v_k = 0, so
+// H_k = I (§II-B).  The fused kernels read the pre-scaled vector
+// u'_k = sqrt(tau_k) v_k, for which H_k z = z - u'_k (u'_k . z).
+#include "hh_internal.cuh"
+
+namespace hh {
+namespace {
+
+constexpr int kPrepThreads = 256;
+
+template <typename T>
+__device__ inline double to_f64(T v) { return (double)v; }
+template <>
+__device__ inline double to_f64<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+// One CTA per reflector: FP64 sum of squares (fixed-order tree), tau, |v|,
+// then the scaled, zero-padded copy in the compute type.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kPrepThreads)
+prepare_reflectors_kernel(const Tin *__restrict__ U, int64_t ldu, int64_t n, int64_t ldv,
+                          Tout *__restrict__ u_out, double *__restrict__ tau,
+                          double *__restrict__ vnorm, int *__restrict__ flag) {
+    __shared__ double red[kPrepThreads];
+    const int64_t k = blockIdx.x;
+    const Tin *v = U + k * ldu;
+    double s = 0.0;
+    bool finite = true;
+    for (int64_t j = threadIdx.x; j < n; j += kPrepThreads) {
+        double x = to_f64(v[j]);
+        finite &= isfinite(x);
+        s += x * x;
+    }
+    if (!finite) atomicOr(flag, 1);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kPrepThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double nn = red[0];
+    const double t = nn > 0.0 ? 2.0 / nn : 0.0;
+    const double scale = sqrt(t);
+    if (threadIdx.x == 0) {
+        tau[k] = t;
+        vnorm[k] = sqrt(nn);
+        if (!isfinite(nn)) atomicOr(flag, 1);
+    }
+    Tout *o = u_out + k * ldv;
+    for (int64_t j = threadIdx.x; j < ldv; j += kPrepThreads)
+        o[j] = j < n ? (Tout)(to_f64(v[j]) * scale) : (Tout)0;
+}
+
+template <typename Tin, typename Tout>
+__global__ void prepare_vectors_kernel(const Tin *__restrict__ d, const int8_t *__restrict__ sign,
+                                       int64_t n, int64_t ldv, Tout *__restrict__ d_out,
+                                       Tout *__restrict__ s_out, int *__restrict__ flag) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ldv;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (d_out) {
+            double x = j < n ? to_f64(d[j]) : 0.0;
+            if (!isfinite(x)) atomicOr(flag, 2);
+            d_out[j] = (Tout)x;
+        }
+        if (s_out) {
+            int s = j < n ? (int)sign[j] : 1;
+            if (s != 1 && s != -1) atomicOr(flag, 4);
+            s_out[j] = (Tout)(s < 0 ? -1.0 : 1.0);
+        }
+    }
+}
+
+template <typename T>
+hh_status prepare_typed(Plan *p, const void *U, int64_t ldu, const void *d, const int8_t *sign,
+                        int *flag, cudaStream_t st) {
+    if (p->h > 0) {
+        prepare_reflectors_kernel<T, T><<<(unsigned)p->h, kPrepThreads, 0, st>>>(
+            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, p->vnorm, flag);
+    }
+    if (d || sign) {
+        int blocks = (int)((p->ldv + 255) / 256);
+        prepare_vectors_kernel<T, T><<<blocks, 256, 0, st>>>(
+            (const T *)d, sign, p->n, p->ldv, (T *)p->d, (T *)p->sign, flag);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "prepare kernels");
+    return HH_OK;
+}
+
+}  // namespace
+
+hh_status prepare_fused(Plan *p, const void *U, int64_t ldu, const void *d, const int8_t *sign,
+                        int *flag, cudaStream_t st) {
+    if (p->dtype == HH_F32) return prepare_typed<float>(p, U, ldu, d, sign, flag, st);
+    if (p->dtype == HH_F64) return prepare_typed<double>(p, U, ldu, d, sign, flag, st);
+    return fail(HH_ERR_UNSUPPORTED, "fused path: dtype must be F32 or F64");
+}
+
+}  // namespace hh
