@@ -198,6 +198,7 @@ def config_dict():
 
 
 def main():
+    global ROWS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -205,7 +206,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="override the batch (profiling a smaller case); not a bench line")
+    ap.add_argument("--rows", default=",".join(ROWS), help="subset of W,WT,SYM to run")
     args = ap.parse_args()
+    ROWS = tuple(r for r in args.rows.split(",") if r)
+    if args.batch:
+        WORKLOAD["batch"] = args.batch
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
