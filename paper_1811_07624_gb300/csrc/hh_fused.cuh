@@ -2,9 +2,9 @@
 //
 // One pass over X: every vector is read once and written once; all h
 // reflectors are applied while the vector sits in registers.  Per reflector
-// (§II-A, Eq. (2), with the pre-scaled u'_k = sqrt(tau_k) v_k):
-//     c = u'_k . x        (warp-shuffle dot product, then across warps)
-//     x <- x - c u'_k
+// (§II-A, Eq. (2): H_k = I - tau_k v_k v_k^T, tau_k = 2 / v_k^T v_k):
+//     c = tau_k (v_k . x)   (warp-shuffle dot product, then across warps)
+//     x <- x - c v_k
 // which is the paper's 4n operations per reflector (§II-A).  The modes run
 // the chain in the orders of Eq. (1) and Eq. (21):
 //     W   : k = h..1, then y = sigma .* x
@@ -15,7 +15,7 @@
 // warps) that share RT rows.  Thread t of a group owns NG 16-byte granules of
 // every one of its rows: granule t + G*i, i < NG, so a warp's loads and stores
 // are 512-byte contiguous runs.  Per reflector a thread loads its NG granules
-// of u'_k once and reuses them for RT rows (dot and update).  The RT partial
+// of v_k once and reuses them for RT rows (dot and update).  The RT partial
 // dot products of a warp are reduced with a transposing shuffle tree (each
 // lane ends with one row's warp sum), then across the group's warps through
 // shared memory with one barrier per reflector (double-buffered).
@@ -112,10 +112,11 @@ struct Cfg {
     static_assert(RT * NW <= 32, "cross-warp reduction uses one lane per (row, warp)");
 };
 
-// Apply one reflector (pre-scaled u') to the RT rows held in x.
+// Apply reflector H_k = I - tk vk vk^T to the RT rows held in x.
 template <typename T, int G, int NG, int RT, int RG>
 __device__ __forceinline__ void reflect(T (&x)[RT][Cfg<T, G, NG, RT, RG>::E],
-                                        const T *__restrict__ uk, int t, int lane, int warp, int rg,
+                                        const T *__restrict__ uk, T tk, int t, int lane, int warp,
+                                        int rg,
                                         T (*red)[RG][RT][Cfg<T, G, NG, RT, RG>::NW], int &buf) {
     using C = Cfg<T, G, NG, RT, RG>;
     constexpr int VEC = C::VEC, E = C::E, NW = C::NW;
@@ -143,7 +144,7 @@ __device__ __forceinline__ void reflect(T (&x)[RT][Cfg<T, G, NG, RT, RG>::E],
     T c[RT];
     if constexpr (NW == 1) {
 #pragma unroll
-        for (int r = 0; r < RT; ++r) c[r] = __shfl_sync(0xffffffffu, v, r << SH);
+        for (int r = 0; r < RT; ++r) c[r] = tk * __shfl_sync(0xffffffffu, v, r << SH);
     } else {
         if ((lane & ((1 << SH) - 1)) == 0) red[buf][rg][lane >> SH][warp] = v;
         __syncthreads();
@@ -152,7 +153,7 @@ __device__ __forceinline__ void reflect(T (&x)[RT][Cfg<T, G, NG, RT, RG>::E],
 #pragma unroll
         for (int off = NW / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
 #pragma unroll
-        for (int r = 0; r < RT; ++r) c[r] = __shfl_sync(0xffffffffu, q, r * NW);
+        for (int r = 0; r < RT; ++r) c[r] = tk * __shfl_sync(0xffffffffu, q, r * NW);
         buf ^= 1;
     }
 #pragma unroll
@@ -183,8 +184,8 @@ __device__ __forceinline__ void scale_cols(T (&x)[RT][Cfg<T, G, NG, RT, RG>::E],
 template <typename T, int MODE, int G, int NG, int RT, int RG>
 __global__ void __launch_bounds__(G *RG)
 fused_chain_kernel(const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch, int n,
-                   const T *__restrict__ U, int64_t ldv, int h, const T *__restrict__ sign,
-                   const T *__restrict__ d, int vec_ok) {
+                   const T *__restrict__ U, const T *__restrict__ tau, int64_t ldv, int h,
+                   const T *__restrict__ sign, const T *__restrict__ d, int vec_ok) {
     using C = Cfg<T, G, NG, RT, RG>;
     constexpr int VEC = C::VEC, E = C::E, NW = C::NW;
     __shared__ T red[2][RG][RT][NW];
@@ -218,12 +219,14 @@ fused_chain_kernel(const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch, in
     if (MODE != HH_MODE_W && sign) scale_cols<T, G, NG, RT, RG>(x, sign, t);
     if (MODE != HH_MODE_W) {
         for (int k = 0; k < h; ++k)
-            reflect<T, G, NG, RT, RG>(x, U + (size_t)k * ldv, t, lane, warp, rg, red, buf);
+            reflect<T, G, NG, RT, RG>(x, U + (size_t)k * ldv, __ldg(tau + k), t, lane, warp, rg,
+                                      red, buf);
     }
     if (MODE == HH_MODE_SYM) scale_cols<T, G, NG, RT, RG>(x, d, t);
     if (MODE != HH_MODE_WT) {
         for (int k = h - 1; k >= 0; --k)
-            reflect<T, G, NG, RT, RG>(x, U + (size_t)k * ldv, t, lane, warp, rg, red, buf);
+            reflect<T, G, NG, RT, RG>(x, U + (size_t)k * ldv, __ldg(tau + k), t, lane, warp, rg,
+                                      red, buf);
     }
     if (MODE != HH_MODE_WT && sign) scale_cols<T, G, NG, RT, RG>(x, sign, t);
 
@@ -255,8 +258,8 @@ fused_chain_kernel(const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch, in
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512)
 wide_chain_kernel(const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch, int64_t n,
-                  const T *__restrict__ U, int64_t ldv, int h, const T *__restrict__ sign,
-                  const T *__restrict__ d) {
+                  const T *__restrict__ U, const T *__restrict__ tau, int64_t ldv, int h,
+                  const T *__restrict__ sign, const T *__restrict__ d) {
     __shared__ T red[32];
     __shared__ T bc;
     const int64_t row = blockIdx.x;
@@ -281,7 +284,7 @@ wide_chain_kernel(const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch, int
         const T *uk = U + (size_t)k * ldv;
         T s = 0;
         for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s = fma(yr[j], uk[j], s);
-        T c = block_sum(s);
+        T c = tau[k] * block_sum(s);
         for (int64_t j = threadIdx.x; j < n; j += blockDim.x) yr[j] = fma(-c, uk[j], yr[j]);
         __syncthreads();
     };
@@ -305,8 +308,8 @@ wide_chain_kernel(const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch, int
 
 template <typename T, int G, int NG, int RT, int RG>
 cudaError_t launch_cfg(hh_mode mode, const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch,
-                       int n, const T *U, int64_t ldv, int h, const T *sign, const T *d,
-                       int vec_ok, cudaStream_t st) {
+                       int n, const T *U, const T *tau, int64_t ldv, int h, const T *sign,
+                       const T *d, int vec_ok, cudaStream_t st) {
     using C = Cfg<T, G, NG, RT, RG>;
     const int64_t blocks = (batch + C::ROWS - 1) / C::ROWS;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -314,15 +317,15 @@ cudaError_t launch_cfg(hh_mode mode, const T *X, int64_t ldx, T *Y, int64_t ldy,
     switch (mode) {
         case HH_MODE_W:
             fused_chain_kernel<T, HH_MODE_W, G, NG, RT, RG>
-                <<<grid, C::THREADS, 0, st>>>(X, ldx, Y, ldy, batch, n, U, ldv, h, sign, d, vec_ok);
+                <<<grid, C::THREADS, 0, st>>>(X, ldx, Y, ldy, batch, n, U, tau, ldv, h, sign, d, vec_ok);
             break;
         case HH_MODE_WT:
             fused_chain_kernel<T, HH_MODE_WT, G, NG, RT, RG>
-                <<<grid, C::THREADS, 0, st>>>(X, ldx, Y, ldy, batch, n, U, ldv, h, sign, d, vec_ok);
+                <<<grid, C::THREADS, 0, st>>>(X, ldx, Y, ldy, batch, n, U, tau, ldv, h, sign, d, vec_ok);
             break;
         default:
             fused_chain_kernel<T, HH_MODE_SYM, G, NG, RT, RG>
-                <<<grid, C::THREADS, 0, st>>>(X, ldx, Y, ldy, batch, n, U, ldv, h, sign, d, vec_ok);
+                <<<grid, C::THREADS, 0, st>>>(X, ldx, Y, ldy, batch, n, U, tau, ldv, h, sign, d, vec_ok);
             break;
     }
     return cudaGetLastError();
@@ -330,19 +333,19 @@ cudaError_t launch_cfg(hh_mode mode, const T *X, int64_t ldx, T *Y, int64_t ldy,
 
 template <typename T>
 cudaError_t launch_wide(hh_mode mode, const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch,
-                        int64_t n, const T *U, int64_t ldv, int h, const T *sign, const T *d,
-                        cudaStream_t st) {
+                        int64_t n, const T *U, const T *tau, int64_t ldv, int h, const T *sign,
+                        const T *d, cudaStream_t st) {
     if (batch > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)batch);
     switch (mode) {
         case HH_MODE_W:
-            wide_chain_kernel<T, HH_MODE_W><<<grid, 512, 0, st>>>(X, ldx, Y, ldy, batch, n, U, ldv, h, sign, d);
+            wide_chain_kernel<T, HH_MODE_W><<<grid, 512, 0, st>>>(X, ldx, Y, ldy, batch, n, U, tau, ldv, h, sign, d);
             break;
         case HH_MODE_WT:
-            wide_chain_kernel<T, HH_MODE_WT><<<grid, 512, 0, st>>>(X, ldx, Y, ldy, batch, n, U, ldv, h, sign, d);
+            wide_chain_kernel<T, HH_MODE_WT><<<grid, 512, 0, st>>>(X, ldx, Y, ldy, batch, n, U, tau, ldv, h, sign, d);
             break;
         default:
-            wide_chain_kernel<T, HH_MODE_SYM><<<grid, 512, 0, st>>>(X, ldx, Y, ldy, batch, n, U, ldv, h, sign, d);
+            wide_chain_kernel<T, HH_MODE_SYM><<<grid, 512, 0, st>>>(X, ldx, Y, ldy, batch, n, U, tau, ldv, h, sign, d);
             break;
     }
     return cudaGetLastError();

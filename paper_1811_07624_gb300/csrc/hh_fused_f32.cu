@@ -5,12 +5,12 @@
 namespace hh {
 
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
-                               int64_t batch, int64_t n, const float *U, int64_t ldv, int h,
+                               int64_t batch, int64_t n, const float *U, const float *tau, int64_t ldv, int h,
                                const float *sign, const float *d, int vec_ok, cudaStream_t st) {
     using namespace fused;
     const int ni = (int)n;
 #define HH_LAUNCH(G, NG, RT, RG) \
-    launch_cfg<float, G, NG, RT, RG>(mode, X, ldx, Y, ldy, batch, ni, U, ldv, h, sign, d, vec_ok, st)
+    launch_cfg<float, G, NG, RT, RG>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, sign, d, vec_ok, st)
     if (n <= 128) return HH_LAUNCH(32, 1, 4, 8);
     if (n <= 256) return HH_LAUNCH(32, 2, 4, 8);
     if (n <= 512) return HH_LAUNCH(32, 4, 4, 8);
@@ -20,7 +20,7 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
     if (n <= 8192) return HH_LAUNCH(512, 4, 2, 1);
     if (n <= 16384) return HH_LAUNCH(1024, 4, 1, 1);
 #undef HH_LAUNCH
-    return launch_wide<float>(mode, X, ldx, Y, ldy, batch, n, U, ldv, h, sign, d, st);
+    return launch_wide<float>(mode, X, ldx, Y, ldy, batch, n, U, tau, ldv, h, sign, d, st);
 }
 
 }  // namespace hh

@@ -33,7 +33,8 @@ struct Plan {
     int device = 0;
     int64_t ldv = 0;        // padded row stride of every stored vector, elements
     // FUSED path, compute dtype (float or double):
-    void *u = nullptr;      // h x ldv, u'_k = sqrt(tau_k) v_k, so H_k z = z - u'_k (u'_k . z)
+    void *u = nullptr;      // h x ldv, v_k as given (zero padded), compute dtype
+    void *tau_t = nullptr;  // h, tau_k rounded to the compute dtype: H_k z = z - tau_k v_k (v_k . z)
     void *d = nullptr;      // ldv, spectrum (zero padded), or null
     void *sign = nullptr;   // ldv, +-1 (one padded), or null
     double *tau = nullptr;  // h, tau_k = 2 / v_k^T v_k (0 for v_k = 0)

@@ -18,12 +18,13 @@ template <>
 __device__ inline double to_f64<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
 // One CTA per reflector: FP64 sum of squares (fixed-order tree), tau, |v|,
-// then the scaled, zero-padded copy in the compute type.
+// then the zero-padded copy in the compute type.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kPrepThreads)
 prepare_reflectors_kernel(const Tin *__restrict__ U, int64_t ldu, int64_t n, int64_t ldv,
                           Tout *__restrict__ u_out, double *__restrict__ tau,
-                          double *__restrict__ vnorm, int *__restrict__ flag) {
+                          Tout *__restrict__ tau_t, double *__restrict__ vnorm,
+                          int *__restrict__ flag) {
     __shared__ double red[kPrepThreads];
     const int64_t k = blockIdx.x;
     const Tin *v = U + k * ldu;
@@ -43,15 +44,15 @@ prepare_reflectors_kernel(const Tin *__restrict__ U, int64_t ldu, int64_t n, int
     }
     const double nn = red[0];
     const double t = nn > 0.0 ? 2.0 / nn : 0.0;
-    const double scale = sqrt(t);
     if (threadIdx.x == 0) {
         tau[k] = t;
+        tau_t[k] = (Tout)t;
         vnorm[k] = sqrt(nn);
         if (!isfinite(nn)) atomicOr(flag, 1);
     }
     Tout *o = u_out + k * ldv;
     for (int64_t j = threadIdx.x; j < ldv; j += kPrepThreads)
-        o[j] = j < n ? (Tout)(to_f64(v[j]) * scale) : (Tout)0;
+        o[j] = j < n ? (Tout)v[j] : (Tout)0;
 }
 
 template <typename Tin, typename Tout>
@@ -78,7 +79,7 @@ hh_status prepare_typed(Plan *p, const void *U, int64_t ldu, const void *d, cons
                         int *flag, cudaStream_t st) {
     if (p->h > 0) {
         prepare_reflectors_kernel<T, T><<<(unsigned)p->h, kPrepThreads, 0, st>>>(
-            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, p->vnorm, flag);
+            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, (T *)p->tau_t, p->vnorm, flag);
     }
     if (d || sign) {
         int blocks = (int)((p->ldv + 255) / 256);
