@@ -288,6 +288,7 @@ def main():
             ev[m].append((a, b))
     t_end.record(stream)
     torch.cuda.synchronize()
+    plan.sync()  # raises if any kernel in the timed region gave up a bounded wait
     if pg:
         pg.barrier()
     clocks = sampler.stop()

@@ -99,6 +99,13 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
 /* Release a plan (NULL is a no-op).  Synchronises the device first. */
 hh_status hh_destroy(hh_plan_t plan);
 
+/*
+ * Synchronise `stream` and report device-side failures of this plan's earlier
+ * calls on it: HH_ERR_TIMEOUT if a kernel gave up a bounded wait (its output
+ * is then incomplete), HH_OK otherwise.  Clears the plan's status word.
+ */
+hh_status hh_sync(hh_plan_t plan, void *stream);
+
 /* Shape and kernel family of a plan.  Any output pointer may be NULL. */
 hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype,
                        hh_path *path);

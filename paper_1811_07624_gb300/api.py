@@ -103,6 +103,10 @@ class Plan:
     def __exit__(self, *exc):
         self.close()
 
+    def sync(self, stream=None) -> None:
+        """Wait for this plan's work on the stream; raise if a kernel timed out."""
+        _lib.call("hh_sync", self._h, _stream_ptr(stream))
+
     @property
     def handle(self) -> ctypes.c_void_p:
         return self._h

@@ -50,6 +50,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->tau);
     cudaFree(p->tau_t);
     cudaFree(p->vnorm);
+    cudaFree(p->err);
     delete p;
 }
 
@@ -155,11 +156,16 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
         (e = cudaMalloc(&p->vnorm, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
         (d && (e = cudaMalloc(&p->d, es * (size_t)p->ldv))) ||
         (sign && (e = cudaMalloc(&p->sign, es * (size_t)p->ldv))) ||
-        (e = cudaMalloc(&flag, sizeof(int)))) {
+        (e = cudaMalloc(&p->err, sizeof(int))) || (e = cudaMalloc(&flag, sizeof(int)))) {
         st = cuda_fail(e, "cudaMalloc (plan)");
         goto done;
     }
-    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s))) {
+    if ((e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev))) {
+        st = cuda_fail(e, "cudaDeviceGetAttribute");
+        goto done;
+    }
+    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) ||
+        (e = cudaMemsetAsync(p->err, 0, sizeof(int), s))) {
         st = cuda_fail(e, "cudaMemsetAsync");
         goto done;
     }
@@ -196,6 +202,22 @@ hh_status hh_destroy(hh_plan_t plan) {
     free_plan(p);
     if (cur != p->device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize (destroy)");
+    return HH_OK;
+}
+
+hh_status hh_sync(hh_plan_t plan, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st = check_plan(p);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int word = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&word, p->err, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemsetAsync(p->err, 0, sizeof(int), s)) || (e = cudaStreamSynchronize(s)))
+        return cuda_fail(e, "hh_sync");
+    if (word == HH_ERR_TIMEOUT)
+        return fail(HH_ERR_TIMEOUT, "a kernel's bounded wait on its bulk copy expired");
+    if (word != 0) return fail(HH_ERR_CUDA, "device status word %d", word);
     return HH_OK;
 }
 

@@ -1,14 +1,30 @@
 // F32 instantiations of the fused chain kernels.  Configurations are picked by
 // the number of columns n; COVER = G * NG * 4 columns per row group.
-#include "hh_fused.cuh"
+#include "hh_staged.cuh"
 
 namespace hh {
 
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                                int64_t batch, int64_t n, const float *U, const float *tau, int64_t ldv, int h,
-                               const float *sign, const float *d, int vec_ok, cudaStream_t st) {
+                               const float *sign, const float *d, int vec_ok, int *err, int num_sms,
+                               cudaStream_t st) {
     using namespace fused;
     const int ni = (int)n;
+    // Aligned rows with n % 4 == 0: persistent kernel with bulk-copy prefetch.
+    if (vec_ok && n % 4 == 0 && n <= 16384) {
+#define HH_STAGED(G, NG, RT, RG)                                                                  \
+    staged::launch<G, NG, RT, RG>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, sign, d, err, \
+                                  num_sms, st)
+        if (n <= 128) return HH_STAGED(32, 1, 8, 16);
+        if (n <= 256) return HH_STAGED(32, 2, 8, 16);
+        if (n <= 512) return HH_STAGED(32, 4, 4, 16);
+        if (n <= 1024) return HH_STAGED(32, 8, 2, 16);
+        if (n <= 2048) return HH_STAGED(64, 8, 2, 8);
+        if (n <= 4096) return HH_STAGED(128, 8, 2, 4);
+        if (n <= 8192) return HH_STAGED(256, 8, 2, 2);
+        return HH_STAGED(512, 8, 2, 1);
+#undef HH_STAGED
+    }
 #define HH_LAUNCH(G, NG, RT, RG) \
     launch_cfg<float, G, NG, RT, RG>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, sign, d, vec_ok, st)
     if (n <= 128) return HH_LAUNCH(32, 1, 4, 8);

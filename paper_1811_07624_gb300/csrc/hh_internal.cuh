@@ -39,6 +39,8 @@ struct Plan {
     void *sign = nullptr;   // ldv, +-1 (one padded), or null
     double *tau = nullptr;  // h, tau_k = 2 / v_k^T v_k (0 for v_k = 0)
     double *vnorm = nullptr;// h, |v_k|
+    int *err = nullptr;     // device status word: a kernel's bounded wait expired (HH_ERR_TIMEOUT)
+    int num_sms = 0;
     // WY path (BF16 storage): filled by wy_prepare
     void *wy = nullptr;
 };

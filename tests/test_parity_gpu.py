@@ -56,6 +56,7 @@ def _check(mode, n, h, batch, dtype, seed=0, with_sign=True, ld_extra=0, offset=
     else:
         out = torch.full((batch, n), float("nan"), dtype=dtype, device=DEV)
         Y = plan.apply_mode(mode, Xg, out=out)
+    plan.sync()  # raises if a kernel gave up a bounded wait
     torch.cuda.synchronize()
     ref = oracle.apply(mode, _as64(torch.as_tensor(U, dtype=dtype)), Xin, sign=s,
                        d=_as64(torch.as_tensor(d, dtype=dtype)))
