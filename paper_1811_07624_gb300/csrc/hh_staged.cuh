@@ -273,13 +273,14 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
     const size_t smem = (size_t)C::ROWS * n * sizeof(float);
     const int64_t tiles = (batch + C::ROWS - 1) / C::ROWS;
     const int grid = (int)(tiles < (int64_t)num_sms ? tiles : (int64_t)num_sms);
+    // The shared-memory opt-in is a per-kernel attribute: one flag per mode.
+    static bool attr_done[3] = {false, false, false};
     auto run = [&](auto kern) -> cudaError_t {
-        static bool attr_done = false;  // set once per instantiation
-        if (!attr_done) {
+        if (!attr_done[mode]) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)(C::ROWS * C::COVER * sizeof(float)));
             if (e != cudaSuccess) return e;
-            attr_done = true;
+            attr_done[mode] = true;
         }
         kern<<<grid, C::THREADS, smem, st>>>(X, ldx, Y, ldy, batch, n, V, tau, ldv, h, sign, d,
                                              err);
