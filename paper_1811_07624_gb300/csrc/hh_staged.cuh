@@ -91,13 +91,26 @@ struct SCfg {
     static_assert(G % 32 == 0 && RT * NW <= 32, "bad staged configuration");
 };
 
+// Pull the cache lines of a reflector a thread group will need soon into L1:
+// a warp's granules of one reflector are NG runs of 512 bytes (4 lines each);
+// lane j < 4*NG fetches line j % 4 of run j / 4.
+template <int G, int NG>
+__device__ __forceinline__ void prefetch_reflector(const float *vk, int warp, int lane) {
+    if (lane < 4 * NG) {
+        const char *p = reinterpret_cast<const char *>(vk) +
+                        16 * ((size_t)warp * 32 + (size_t)G * (lane >> 2)) + 128 * (lane & 3);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    }
+}
+
 template <int G, int NG, int RT, int RG>
 __device__ __forceinline__ void reflect2(float2 (&x)[RT][SCfg<G, NG, RT, RG>::E2],
-                                         const float *__restrict__ vk, float tk, int t, int lane,
-                                         int warp, int rg,
+                                         const float *__restrict__ vk, float tk,
+                                         const float *vpre, int t, int lane, int warp, int rg,
                                          float (*red)[RG][RT][SCfg<G, NG, RT, RG>::NW], int &buf) {
     using C = SCfg<G, NG, RT, RG>;
     constexpr int E2 = C::E2, NW = C::NW;
+    if (vpre) prefetch_reflector<G, NG>(vpre, warp, lane);
     float2 u[E2];
 #pragma unroll
     for (int i = 0; i < NG; ++i) {
@@ -237,12 +250,16 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
         // symmetric mode within the register budget): W runs k = h..1, W^T runs
         // k = 1..h, S runs k = 1..h, scales by d, then k = h..1.
         const int steps = MODE == HH_MODE_SYM ? 2 * h : h;
+        auto kof = [&](int s) {
+            return MODE == HH_MODE_W ? h - 1 - s
+                                     : (MODE == HH_MODE_WT ? s : (s < h ? s : 2 * h - 1 - s));
+        };
         for (int s = 0; s < steps; ++s) {
             if (MODE == HH_MODE_SYM && s == h) scale2<G, NG, RT, RG>(x, d, t);
-            const int k = MODE == HH_MODE_W ? h - 1 - s
-                                            : (MODE == HH_MODE_WT ? s : (s < h ? s : 2 * h - 1 - s));
-            reflect2<G, NG, RT, RG>(x, V + (size_t)k * ldv, __ldg(tau + k), t, lane, warp, rg,
-                                    red, buf);
+            const int k = kof(s);
+            const float *vpre = s + 2 < steps ? V + (size_t)kof(s + 2) * ldv : nullptr;
+            reflect2<G, NG, RT, RG>(x, V + (size_t)k * ldv, __ldg(tau + k), vpre, t, lane, warp,
+                                    rg, red, buf);
         }
         if (MODE == HH_MODE_SYM && h == 0) scale2<G, NG, RT, RG>(x, d, t);
         if (MODE != HH_MODE_WT && sign) scale2<G, NG, RT, RG>(x, sign, t);
