@@ -16,13 +16,15 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
     staged::launch<G, NG, RT, RG>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, sign, d, err, \
                                   num_sms, st)
         // (G, NG, RT, RG): 4 rows per thread where the register budget allows, so
-        // each loaded reflector value feeds 8 FMAs (dot + update over 4 rows).
-        if (n <= 128) return HH_STAGED(32, 1, 8, 16);
-        if (n <= 256) return HH_STAGED(32, 2, 8, 16);
-        if (n <= 512) return HH_STAGED(32, 4, 4, 16);
-        if (n <= 1024) return HH_STAGED(64, 4, 4, 8);
-        if (n <= 2048) return HH_STAGED(128, 4, 4, 4);
-        if (n <= 4096) return HH_STAGED(256, 4, 4, 2);
+        // each loaded reflector value feeds 8 FMAs (dot + update over 4 rows);
+        // small CTAs, several resident per SM, so one CTA's loads and stores
+        // overlap another's arithmetic.
+        if (n <= 128) return HH_STAGED(32, 1, 8, 4);
+        if (n <= 256) return HH_STAGED(32, 2, 8, 4);
+        if (n <= 512) return HH_STAGED(32, 4, 4, 4);
+        if (n <= 1024) return HH_STAGED(64, 4, 4, 2);
+        if (n <= 2048) return HH_STAGED(128, 4, 4, 1);
+        if (n <= 4096) return HH_STAGED(256, 4, 4, 1);
         if (n <= 8192) return HH_STAGED(512, 4, 2, 1);
         return HH_STAGED(512, 8, 2, 1);
 #undef HH_STAGED

@@ -6,7 +6,7 @@
 // mode orders of Eq. (1) / Eq. (21).  Each vector is read from HBM once (into
 // shared memory, then registers) and written once (registers -> HBM).
 //
-// Layout: persistent CTAs (one per SM), RG row groups of G threads; thread t of
+// Layout: persistent CTAs (as many per SM as fit), RG row groups of G threads; thread t of
 // a group owns granules t + G*i (i < NG) of 4 floats of each of its RT rows.
 // Within a group the RT partial dot products are reduced by a transposing warp
 // shuffle, then across the group's G/32 warps through shared memory behind a
@@ -172,7 +172,7 @@ __device__ __forceinline__ void scale2(float2 (&x)[RT][SCfg<G, NG, RT, RG>::E2],
 // Requirements (checked by the launcher): n % 4 == 0, n <= COVER, X rows and
 // base 16-byte aligned, ROWS * n * 4 bytes of dynamic shared memory.
 template <int MODE, int G, int NG, int RT, int RG>
-__global__ void __launch_bounds__(G *RG, 1)
+__global__ void __launch_bounds__(G *RG)
 staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t batch, int n,
                     const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv,
                     int h, const float *__restrict__ sign, const float *__restrict__ d,
@@ -289,16 +289,24 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
     using C = SCfg<G, NG, RT, RG>;
     const size_t smem = (size_t)C::ROWS * n * sizeof(float);
     const int64_t tiles = (batch + C::ROWS - 1) / C::ROWS;
-    const int grid = (int)(tiles < (int64_t)num_sms ? tiles : (int64_t)num_sms);
-    // The shared-memory opt-in is a per-kernel attribute: one flag per mode.
+    // The shared-memory opt-in and the resident-CTA count are per kernel: one
+    // entry per mode, filled on first use (the count at the largest stage).
     static bool attr_done[3] = {false, false, false};
+    static int per_sm[3] = {0, 0, 0};
     auto run = [&](auto kern) -> cudaError_t {
         if (!attr_done[mode]) {
+            const size_t smax = (size_t)C::ROWS * C::COVER * sizeof(float);
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(C::ROWS * C::COVER * sizeof(float)));
+                                                 (int)smax);
             if (e != cudaSuccess) return e;
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::THREADS, smax);
+            if (e != cudaSuccess) return e;
+            per_sm[mode] = nb > 0 ? nb : 1;
             attr_done[mode] = true;
         }
+        const int64_t slots = (int64_t)num_sms * per_sm[mode];
+        const int grid = (int)(tiles < slots ? tiles : slots);
         kern<<<grid, C::THREADS, smem, st>>>(X, ldx, Y, ldy, batch, n, V, tau, ldv, h, sign, d,
                                              err);
         return cudaGetLastError();
