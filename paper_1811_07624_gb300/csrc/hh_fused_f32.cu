@@ -10,23 +10,23 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
                                cudaStream_t st) {
     using namespace fused;
     const int ni = (int)n;
-    // Aligned rows with n % 4 == 0: persistent kernel with bulk-copy prefetch.
-    if (vec_ok && n % 4 == 0 && n <= 16384) {
-#define HH_STAGED(G, NG, RT, RG)                                                                  \
+    // Aligned rows with n % 4 == 0: persistent kernel, tiles and reflectors
+    // staged through shared memory by bulk copies.
+    if (vec_ok && n % 4 == 0 && n <= 8192) {
+#define HH_STAGED(G, NG, RT, RG, KB)                                                              \
     staged::launch<G, NG, RT, RG>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, sign, d, err, \
-                                  num_sms, st)
-        // (G, NG, RT, RG): 4 rows per thread where the register budget allows, so
-        // each loaded reflector value feeds 8 FMAs (dot + update over 4 rows);
-        // small CTAs, several resident per SM, so one CTA's loads and stores
-        // overlap another's arithmetic.
-        if (n <= 128) return HH_STAGED(32, 1, 8, 4);
-        if (n <= 256) return HH_STAGED(32, 2, 8, 4);
-        if (n <= 512) return HH_STAGED(32, 4, 4, 4);
-        if (n <= 1024) return HH_STAGED(64, 4, 4, 2);
-        if (n <= 2048) return HH_STAGED(128, 4, 4, 1);
-        if (n <= 4096) return HH_STAGED(256, 4, 4, 1);
-        if (n <= 8192) return HH_STAGED(512, 4, 2, 1);
-        return HH_STAGED(512, 8, 2, 1);
+                                  num_sms, (size_t)(KB) * 1024, st)
+        // (G, NG, RT, RG, shared-memory budget per CTA in KB): 4 rows per thread
+        // where the register budget allows, so each reflector value read from
+        // shared memory feeds 8 FMAs; the budget leaves room for the number of
+        // CTAs per SM that the registers allow (8, 4, 2 or 1).
+        if (n <= 128) return HH_STAGED(32, 1, 8, 4, 54);
+        if (n <= 256) return HH_STAGED(32, 2, 8, 4, 54);
+        if (n <= 512) return HH_STAGED(32, 4, 4, 4, 54);
+        if (n <= 1024) return HH_STAGED(64, 4, 4, 1, 26);
+        if (n <= 2048) return HH_STAGED(128, 4, 4, 1, 54);
+        if (n <= 4096) return HH_STAGED(256, 4, 4, 1, 110);
+        return HH_STAGED(512, 4, 2, 1, 224);
 #undef HH_STAGED
     }
 #define HH_LAUNCH(G, NG, RT, RG) \

@@ -1,21 +1,30 @@
 // Staged F32 reflector-chain kernel: the fused chain of hh_fused.cuh with the
-// next tile of vectors prefetched into shared memory by the bulk-copy engine
-// (cp.async.bulk + mbarrier) while the current tile is computed in registers.
+// vectors and the reflectors moved through shared memory by the bulk-copy
+// engine (cp.async.bulk + mbarrier), so the arithmetic loop reads registers
+// and shared memory only.
 //
 // Per reflector (§II-A, Eq. (2)): c = tau_k (v_k . x), x <- x - c v_k, in the
 // mode orders of Eq. (1) / Eq. (21).  Each vector is read from HBM once (into
 // shared memory, then registers) and written once (registers -> HBM).
 //
-// Layout: persistent CTAs (as many per SM as fit), RG row groups of G threads; thread t of
-// a group owns granules t + G*i (i < NG) of 4 floats of each of its RT rows.
-// Within a group the RT partial dot products are reduced by a transposing warp
-// shuffle, then across the group's G/32 warps through shared memory behind a
-// named barrier (one per group, so groups run independently).  Arithmetic on
-// pairs of columns uses the packed FP32 FMA (fma.rn.f32x2).
+// Layout.  Persistent CTAs, as many per SM as fit.  A CTA is RG row groups of
+// G threads; thread t of a group owns granules t + G*i (i < NG) of 4 floats of
+// each of its RT rows, so one reflector value loaded from shared memory feeds
+// 2*RT FMAs.  The RT partial dot products are reduced by a transposing warp
+// shuffle, then across the group's G/32 warps through shared memory behind one
+// CTA barrier per chain step.  Pairs of columns use the packed FP32 FMA.
 //
-// Waits on the mbarrier are bounded (~1 s of clock cycles); on expiry the
-// kernel records HH_ERR_TIMEOUT in *err, waits once more (bounded) for its
-// copy, and returns.
+// Shared memory: `stage` receives the CTA's next tile of rows while the
+// current tile is computed in registers.  `ring` holds reflector vectors
+// (padded to COVER floats): when all h fit (resident) they are loaded once per
+// CTA; otherwise S slots stream the chain steps, and the slot used by step
+// g-1 is refilled (with step g-1+S) right after step g's barrier, which every
+// thread passes only after it finished step g-1.
+//
+// Waits on an mbarrier are bounded (about a second of clock cycles).  On
+// expiry the kernel records HH_ERR_TIMEOUT in *err, waits once more (bounded)
+// for that copy, marks the CTA aborted so no further wait blocks, and runs to
+// the end without trusting its data.
 #pragma once
 
 #include "hh_fused.cuh"
@@ -24,6 +33,7 @@ namespace hh {
 namespace staged {
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int kMaxSlots = 64;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -52,8 +62,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: true when the phase with the given parity completed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > kWaitCycles) return false;
@@ -76,10 +86,6 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ void named_bar(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 template <int G, int NG, int RT, int RG>
 struct SCfg {
     static constexpr int E = NG * 4;      // floats of one row held by a thread
@@ -87,71 +93,15 @@ struct SCfg {
     static constexpr int NW = G / 32;
     static constexpr int THREADS = G * RG;
     static constexpr int ROWS = RT * RG;  // rows per tile
-    static constexpr int COVER = G * E;
+    static constexpr int COVER = G * E;   // padded reflector length in shared memory
     static_assert(G % 32 == 0 && RT * NW <= 32, "bad staged configuration");
+    static_assert(RG == 1 || NW == 1, "several row groups only with one warp each");
 };
 
-// Pull the cache lines of a reflector a thread group will need soon into L1:
-// a warp's granules of one reflector are NG runs of 512 bytes (4 lines each);
-// lane j < 4*NG fetches line j % 4 of run j / 4.
-template <int G, int NG>
-__device__ __forceinline__ void prefetch_reflector(const float *vk, int warp, int lane) {
-    if (lane < 4 * NG) {
-        const char *p = reinterpret_cast<const char *>(vk) +
-                        16 * ((size_t)warp * 32 + (size_t)G * (lane >> 2)) + 128 * (lane & 3);
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-    }
-}
-
+// Floats of the tile stage (ROWS rows of n), rounded up to 128 bytes.
 template <int G, int NG, int RT, int RG>
-__device__ __forceinline__ void reflect2(float2 (&x)[RT][SCfg<G, NG, RT, RG>::E2],
-                                         const float *__restrict__ vk, float tk,
-                                         const float *vpre, int t, int lane, int warp, int rg,
-                                         float (*red)[RG][RT][SCfg<G, NG, RT, RG>::NW], int &buf) {
-    using C = SCfg<G, NG, RT, RG>;
-    constexpr int E2 = C::E2, NW = C::NW;
-    if (vpre) prefetch_reflector<G, NG>(vpre, warp, lane);
-    float2 u[E2];
-#pragma unroll
-    for (int i = 0; i < NG; ++i) {
-        float4 q = __ldg(reinterpret_cast<const float4 *>(vk) + (t + G * i));
-        u[2 * i] = make_float2(q.x, q.y);
-        u[2 * i + 1] = make_float2(q.z, q.w);
-    }
-    float p[RT];
-#pragma unroll
-    for (int r = 0; r < RT; ++r) {
-        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int e = 0; e < E2; e += 2) {
-            a = __ffma2_rn(x[r][e], u[e], a);
-            if (e + 1 < E2) b = __ffma2_rn(x[r][e + 1], u[e + 1], b);
-        }
-        a = __fadd2_rn(a, b);
-        p[r] = a.x + a.y;
-    }
-    float v = fused::warp_reduce_rows<float, RT>(p, lane);
-    constexpr int SH = 5 - fused::ilog2(RT);
-    float c[RT];
-    if constexpr (NW == 1) {
-#pragma unroll
-        for (int r = 0; r < RT; ++r) c[r] = -tk * __shfl_sync(0xffffffffu, v, r << SH);
-    } else {
-        if ((lane & ((1 << SH) - 1)) == 0) red[buf][rg][lane >> SH][warp] = v;
-        named_bar(1 + rg, G);
-        float q = lane < RT * NW ? red[buf][rg][lane / NW][lane % NW] : 0.f;
-#pragma unroll
-        for (int off = NW / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
-#pragma unroll
-        for (int r = 0; r < RT; ++r) c[r] = -tk * __shfl_sync(0xffffffffu, q, r * NW);
-        buf ^= 1;
-    }
-#pragma unroll
-    for (int r = 0; r < RT; ++r) {
-        const float2 cc = make_float2(c[r], c[r]);
-#pragma unroll
-        for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(u[e], cc, x[r][e]);
-    }
+__host__ __device__ constexpr size_t stage_floats(int n) {
+    return ((size_t)SCfg<G, NG, RT, RG>::ROWS * n + 31) / 32 * 32;
 }
 
 template <int G, int NG, int RT, int RG>
@@ -169,20 +119,24 @@ __device__ __forceinline__ void scale2(float2 (&x)[RT][SCfg<G, NG, RT, RG>::E2],
     }
 }
 
-// Requirements (checked by the launcher): n % 4 == 0, n <= COVER, X rows and
-// base 16-byte aligned, ROWS * n * 4 bytes of dynamic shared memory.
+// Requirements (checked by the launcher): n % 4 == 0, n <= COVER, X and Y rows
+// and bases 16-byte aligned, V rows padded with zeros to ldv >= COVER, ldv % 4
+// == 0, 1 <= S <= kMaxSlots, and stage + S*COVER floats of dynamic shared memory.
 template <int MODE, int G, int NG, int RT, int RG>
 __global__ void __launch_bounds__(G *RG)
 staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t batch, int n,
                     const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv,
-                    int h, const float *__restrict__ sign, const float *__restrict__ d,
+                    int h, const float *__restrict__ sign, const float *__restrict__ d, int S,
                     int *__restrict__ err) {
     using C = SCfg<G, NG, RT, RG>;
-    constexpr int E2 = C::E2, NW = C::NW, ROWS = C::ROWS;
-    extern __shared__ __align__(128) float stage[];  // ROWS x n
+    constexpr int E2 = C::E2, NW = C::NW, ROWS = C::ROWS, COVER = C::COVER;
+    extern __shared__ __align__(128) float smem[];
+    float *stage = smem;                                  // ROWS x n
+    float *ring = smem + stage_floats<G, NG, RT, RG>(n);  // S x COVER
     __shared__ __align__(8) uint64_t full_bar;
+    __shared__ __align__(8) uint64_t vbar[kMaxSlots];
     __shared__ float red[2][RG][RT][NW];
-    __shared__ int abort_flag;
+    __shared__ int aborted;
 
     const int tid = threadIdx.x;
     const int rg = tid / G;
@@ -192,8 +146,15 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
     int64_t tile = blockIdx.x;
     if (tile >= tiles) return;
     const uint32_t row_bytes = (uint32_t)n * 4u;
-
-    auto issue = [&](int64_t tl) {
+    const bool resident = S >= h;
+    const int steps = MODE == HH_MODE_SYM ? 2 * h : h;
+    const int64_t my_tiles = (tiles - 1 - blockIdx.x) / gridDim.x + 1;
+    const int64_t total_steps = my_tiles * steps;
+    auto kof = [&](int s) {
+        return MODE == HH_MODE_W ? h - 1 - s
+                                 : (MODE == HH_MODE_WT ? s : (s < h ? s : 2 * h - 1 - s));
+    };
+    auto issue_tile = [&](int64_t tl) {
         const int64_t r0 = tl * ROWS;
         const int64_t left = batch - r0;
         const int nvalid = left < ROWS ? (int)left : ROWS;
@@ -201,27 +162,40 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
         for (int r = 0; r < nvalid; ++r)
             bulk_g2s(stage + (size_t)r * n, X + (r0 + r) * ldx, row_bytes, &full_bar);
     };
+    auto issue_reflector = [&](int k, int slot) {
+        mbar_expect_tx(&vbar[slot], COVER * 4u);
+        bulk_g2s(ring + (size_t)slot * COVER, V + (size_t)k * ldv, COVER * 4u, &vbar[slot]);
+    };
+    auto wait = [&](uint64_t *bar, uint32_t parity) {
+        if (*(volatile int *)&aborted) return;
+        if (!mbar_wait_bounded(bar, parity)) {
+            atomicExch(err, (int)HH_ERR_TIMEOUT);
+            mbar_wait_bounded(bar, parity);  // give the copy in flight one more chance to land
+            *(volatile int *)&aborted = 1;
+        }
+    };
 
     if (tid == 0) {
-        abort_flag = 0;
+        aborted = 0;
         mbar_init(&full_bar, 1);
+        const int nslots = resident ? (h > 0 ? h : 1) : S;
+        for (int j = 0; j < nslots; ++j) mbar_init(&vbar[j], 1);
         fence_proxy_async();
-        issue(tile);
+        issue_tile(tile);
+        if (resident) {
+            for (int k = 0; k < h; ++k) issue_reflector(k, k);
+        } else {
+            for (int64_t gg = 0; gg < S && gg < total_steps; ++gg)
+                issue_reflector(kof((int)(gg % steps)), (int)gg);
+        }
     }
     __syncthreads();
 
     uint32_t phase = 0;
     int buf = 0;
+    int64_t g = 0;  // this CTA's chain-step counter
     for (; tile < tiles; tile += gridDim.x) {
-        const bool ok = mbar_wait_bounded(&full_bar, phase);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(err, (int)HH_ERR_TIMEOUT);
-                mbar_wait_bounded(&full_bar, phase);  // let the copy in flight land
-            }
-            __syncthreads();
-            return;
-        }
+        wait(&full_bar, phase);
         phase ^= 1;
         const int64_t r0 = tile * ROWS;
         float2 x[RT][E2];
@@ -242,24 +216,66 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
         __syncthreads();  // every thread has its rows: the stage may be refilled
         if (tid == 0 && tile + gridDim.x < tiles) {
             fence_proxy_async();
-            issue(tile + gridDim.x);
+            issue_tile(tile + gridDim.x);
         }
 
         if (MODE != HH_MODE_W && sign) scale2<G, NG, RT, RG>(x, sign, t);
-        // One loop over the chain steps of the mode (a single loop body keeps the
-        // symmetric mode within the register budget): W runs k = h..1, W^T runs
-        // k = 1..h, S runs k = 1..h, scales by d, then k = h..1.
-        const int steps = MODE == HH_MODE_SYM ? 2 * h : h;
-        auto kof = [&](int s) {
-            return MODE == HH_MODE_W ? h - 1 - s
-                                     : (MODE == HH_MODE_WT ? s : (s < h ? s : 2 * h - 1 - s));
-        };
-        for (int s = 0; s < steps; ++s) {
+        for (int s = 0; s < steps; ++s, ++g) {
             if (MODE == HH_MODE_SYM && s == h) scale2<G, NG, RT, RG>(x, d, t);
             const int k = kof(s);
-            const float *vpre = s + 2 < steps ? V + (size_t)kof(s + 2) * ldv : nullptr;
-            reflect2<G, NG, RT, RG>(x, V + (size_t)k * ldv, __ldg(tau + k), vpre, t, lane, warp,
-                                    rg, red, buf);
+            const int slot = resident ? k : (int)(g % S);
+            wait(&vbar[slot], resident ? 0u : (uint32_t)((g / S) & 1));
+            const float4 *vk = reinterpret_cast<const float4 *>(ring + (size_t)slot * COVER);
+            float2 u[E2];
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const float4 q = vk[t + G * i];
+                u[2 * i] = make_float2(q.x, q.y);
+                u[2 * i + 1] = make_float2(q.z, q.w);
+            }
+            float p[RT];
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < E2; e += 2) {
+                    a = __ffma2_rn(x[r][e], u[e], a);
+                    if (e + 1 < E2) b = __ffma2_rn(x[r][e + 1], u[e + 1], b);
+                }
+                a = __fadd2_rn(a, b);
+                p[r] = a.x + a.y;
+            }
+            const float tk = __ldg(tau + k);
+            float v = fused::warp_reduce_rows<float, RT>(p, lane);
+            constexpr int SH = 5 - fused::ilog2(RT);
+            float c[RT];
+            if constexpr (NW > 1) {
+                if ((lane & ((1 << SH) - 1)) == 0) red[buf][rg][lane >> SH][warp] = v;
+            }
+            if (NW > 1 || !resident) __syncthreads();
+            // every thread finished step g-1: its slot may be refilled with step g-1+S
+            if (!resident && tid == 0 && g >= 1 && g - 1 + S < total_steps) {
+                fence_proxy_async();
+                const int64_t gn = g - 1 + S;
+                issue_reflector(kof((int)(gn % steps)), (int)((g - 1) % S));
+            }
+            if constexpr (NW == 1) {
+#pragma unroll
+                for (int r = 0; r < RT; ++r) c[r] = -tk * __shfl_sync(0xffffffffu, v, r << SH);
+            } else {
+                float q = lane < RT * NW ? red[buf][rg][lane / NW][lane % NW] : 0.f;
+#pragma unroll
+                for (int off = NW / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+#pragma unroll
+                for (int r = 0; r < RT; ++r) c[r] = -tk * __shfl_sync(0xffffffffu, q, r * NW);
+                buf ^= 1;
+            }
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const float2 cc = make_float2(c[r], c[r]);
+#pragma unroll
+                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(u[e], cc, x[r][e]);
+            }
         }
         if (MODE == HH_MODE_SYM && h == 0) scale2<G, NG, RT, RG>(x, d, t);
         if (MODE != HH_MODE_WT && sign) scale2<G, NG, RT, RG>(x, sign, t);
@@ -279,35 +295,49 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
             }
         }
     }
-    (void)abort_flag;
+}
+
+// Slots of the reflector ring: all h when they fit in `budget` bytes next to
+// the stage (loaded once per CTA), else as many as fit, at least 2.
+template <int G, int NG, int RT, int RG>
+int ring_slots(int n, int h, size_t budget) {
+    using C = SCfg<G, NG, RT, RG>;
+    const size_t st = stage_floats<G, NG, RT, RG>(n) * sizeof(float);
+    const size_t slot = (size_t)C::COVER * sizeof(float);
+    if (h <= kMaxSlots && st + (size_t)h * slot <= budget) return h > 0 ? h : 1;
+    long long s = budget > st ? (long long)((budget - st) / slot) : 0;
+    if (s < 2) s = 2;
+    if (s > kMaxSlots) s = kMaxSlots;
+    return (int)s;
 }
 
 template <int G, int NG, int RT, int RG>
 cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                    int64_t batch, int n, const float *V, const float *tau, int64_t ldv, int h,
-                   const float *sign, const float *d, int *err, int num_sms, cudaStream_t st) {
+                   const float *sign, const float *d, int *err, int num_sms, size_t budget,
+                   cudaStream_t st) {
     using C = SCfg<G, NG, RT, RG>;
-    const size_t smem = (size_t)C::ROWS * n * sizeof(float);
+    const int S = ring_slots<G, NG, RT, RG>(n, h, budget);
+    const size_t smem = (stage_floats<G, NG, RT, RG>(n) + (size_t)S * C::COVER) * sizeof(float);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const int64_t tiles = (batch + C::ROWS - 1) / C::ROWS;
-    // The shared-memory opt-in and the resident-CTA count are per kernel: one
-    // entry per mode, filled on first use (the count at the largest stage).
+    // The shared-memory opt-in is a per-kernel attribute (one flag per mode);
+    // the resident-CTA count depends on this call's shared memory.
     static bool attr_done[3] = {false, false, false};
-    static int per_sm[3] = {0, 0, 0};
     auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e;
         if (!attr_done[mode]) {
-            const size_t smax = (size_t)C::ROWS * C::COVER * sizeof(float);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smax);
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return e;
-            int nb = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::THREADS, smax);
-            if (e != cudaSuccess) return e;
-            per_sm[mode] = nb > 0 ? nb : 1;
             attr_done[mode] = true;
         }
-        const int64_t slots = (int64_t)num_sms * per_sm[mode];
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::THREADS, smem);
+        if (e != cudaSuccess) return e;
+        if (nb < 1) return cudaErrorInvalidConfiguration;
+        const int64_t slots = (int64_t)num_sms * nb;
         const int grid = (int)(tiles < slots ? tiles : slots);
-        kern<<<grid, C::THREADS, smem, st>>>(X, ldx, Y, ldy, batch, n, V, tau, ldv, h, sign, d,
+        kern<<<grid, C::THREADS, smem, st>>>(X, ldx, Y, ldy, batch, n, V, tau, ldv, h, sign, d, S,
                                              err);
         return cudaGetLastError();
     };
