@@ -319,17 +319,18 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
     using C = SCfg<G, NG, RT, RG>;
     const int S = ring_slots<G, NG, RT, RG>(n, h, budget);
     const size_t smem = (stage_floats<G, NG, RT, RG>(n) + (size_t)S * C::COVER) * sizeof(float);
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (smem > 226 * 1024) return cudaErrorInvalidConfiguration;
     const int64_t tiles = (batch + C::ROWS - 1) / C::ROWS;
-    // The shared-memory opt-in is a per-kernel attribute (one flag per mode);
-    // the resident-CTA count depends on this call's shared memory.
-    static bool attr_done[3] = {false, false, false};
+    // The shared-memory opt-in is a per-kernel attribute (one entry per mode),
+    // raised when a call needs more than any earlier one; the resident-CTA
+    // count depends on this call's shared memory.
+    static size_t attr_set[3] = {0, 0, 0};
     auto run = [&](auto kern) -> cudaError_t {
         cudaError_t e;
-        if (!attr_done[mode]) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (smem > attr_set[mode]) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            attr_done[mode] = true;
+            attr_set[mode] = smem;
         }
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::THREADS, smem);
