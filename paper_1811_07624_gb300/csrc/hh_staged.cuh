@@ -185,8 +185,11 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
         if (resident) {
             for (int k = 0; k < h; ++k) issue_reflector(k, k);
         } else {
-            for (int64_t gg = 0; gg < S && gg < total_steps; ++gg)
-                issue_reflector(kof((int)(gg % steps)), (int)gg);
+            int si = 0;
+            for (int64_t gg = 0; gg < S && gg < total_steps; ++gg) {
+                issue_reflector(kof(si), (int)gg);
+                si = si + 1 == steps ? 0 : si + 1;
+            }
         }
     }
     __syncthreads();
@@ -194,6 +197,13 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
     uint32_t phase = 0;
     int buf = 0;
     int64_t g = 0;  // this CTA's chain-step counter
+    // Ring bookkeeping without divisions: the slot and phase parity of the
+    // current step, the slot of the previous step, and (thread 0) the next
+    // global step to copy in and its position in the chain.
+    int slot_c = 0, slot_prev = 0;
+    uint32_t par_c = 0;
+    int64_t g_issue = S;
+    int s_issue = steps > 0 ? S % steps : 0;
     for (; tile < tiles; tile += gridDim.x) {
         wait(&full_bar, phase);
         phase ^= 1;
@@ -223,8 +233,8 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
         for (int s = 0; s < steps; ++s, ++g) {
             if (MODE == HH_MODE_SYM && s == h) scale2<G, NG, RT, RG>(x, d, t);
             const int k = kof(s);
-            const int slot = resident ? k : (int)(g % S);
-            wait(&vbar[slot], resident ? 0u : (uint32_t)((g / S) & 1));
+            const int slot = resident ? k : slot_c;
+            wait(&vbar[slot], resident ? 0u : par_c);
             const float4 *vk = reinterpret_cast<const float4 *>(ring + (size_t)slot * COVER);
             float2 u[E2];
 #pragma unroll
@@ -254,10 +264,18 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
             }
             if (NW > 1 || !resident) __syncthreads();
             // every thread finished step g-1: its slot may be refilled with step g-1+S
-            if (!resident && tid == 0 && g >= 1 && g - 1 + S < total_steps) {
+            if (!resident && tid == 0 && g >= 1 && g_issue < total_steps) {
                 fence_proxy_async();
-                const int64_t gn = g - 1 + S;
-                issue_reflector(kof((int)(gn % steps)), (int)((g - 1) % S));
+                issue_reflector(kof(s_issue), slot_prev);
+                ++g_issue;
+                s_issue = s_issue + 1 == steps ? 0 : s_issue + 1;
+            }
+            if (!resident) {
+                slot_prev = slot_c;
+                if (++slot_c == S) {
+                    slot_c = 0;
+                    par_c ^= 1u;
+                }
             }
             if constexpr (NW == 1) {
 #pragma unroll
