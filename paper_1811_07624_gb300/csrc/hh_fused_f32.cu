@@ -6,27 +6,25 @@ namespace hh {
 
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                                int64_t batch, int64_t n, const float *U, const float *tau, int64_t ldv, int h,
-                               const float *sign, const float *d, int vec_ok, int *err, int num_sms,
-                               cudaStream_t st) {
+                               const float *gram, const float *sign, const float *d, int vec_ok,
+                               int *err, int num_sms, cudaStream_t st) {
     using namespace fused;
     const int ni = (int)n;
-    // Aligned rows with n % 4 == 0: persistent kernel, tiles and reflectors
-    // staged through shared memory by bulk copies.
+    // Aligned rows with n % 4 == 0: persistent blocked kernel, tiles prefetched
+    // into shared memory by bulk copies.
     if (vec_ok && n % 4 == 0 && n <= 8192) {
-#define HH_STAGED(G, NG, RT, RG, KB)                                                              \
-    staged::launch<G, NG, RT, RG>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, sign, d, err, \
-                                  num_sms, (size_t)(KB) * 1024, st)
-        // (G, NG, RT, RG, shared-memory budget per CTA in KB): 4 rows per thread
-        // where the register budget allows, so each reflector value read from
-        // shared memory feeds 8 FMAs; the budget leaves room for the number of
-        // CTAs per SM that the registers allow (8, 4, 2 or 1).
-        if (n <= 128) return HH_STAGED(32, 1, 8, 4, 54);
-        if (n <= 256) return HH_STAGED(32, 2, 8, 4, 54);
-        if (n <= 512) return HH_STAGED(32, 4, 4, 4, 54);
-        if (n <= 1024) return HH_STAGED(64, 4, 4, 1, 26);
-        if (n <= 2048) return HH_STAGED(128, 4, 4, 1, 54);
-        if (n <= 4096) return HH_STAGED(256, 4, 4, 1, 110);
-        return HH_STAGED(512, 4, 2, 1, 224);
+#define HH_STAGED(G, NG, RT, RG, B)                                                            \
+    staged::launch<G, NG, RT, RG, B>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, \
+                                     d, err, num_sms, st)
+        // (G, NG, RT, RG, B): 4 rows per thread where the register budget allows,
+        // so each loaded reflector value feeds 8 FMAs; B reflectors per round.
+        if (n <= 128) return HH_STAGED(32, 1, 8, 4, 2);
+        if (n <= 256) return HH_STAGED(32, 2, 8, 4, 2);
+        if (n <= 512) return HH_STAGED(32, 4, 4, 4, 2);
+        if (n <= 1024) return HH_STAGED(64, 4, 4, 1, 2);
+        if (n <= 2048) return HH_STAGED(128, 4, 4, 1, 2);
+        if (n <= 4096) return HH_STAGED(256, 4, 4, 1, 2);
+        return HH_STAGED(512, 4, 2, 1, 2);
 #undef HH_STAGED
     }
 #define HH_LAUNCH(G, NG, RT, RG) \
