@@ -2,6 +2,15 @@
 // the number of columns n; COVER = G * NG * 4 columns per row group.
 #include "hh_staged.cuh"
 
+// Tuned (G, NG, RT, RG, B) of the n <= 4096 staged configuration.
+#ifndef HH_N4096_G
+#define HH_N4096_G 256
+#define HH_N4096_NG 4
+#define HH_N4096_RT 4
+#define HH_N4096_RG 1
+#define HH_N4096_B 2
+#endif
+
 namespace hh {
 
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
@@ -23,7 +32,7 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
         if (n <= 512) return HH_STAGED(32, 4, 4, 4, 2);
         if (n <= 1024) return HH_STAGED(64, 4, 4, 1, 2);
         if (n <= 2048) return HH_STAGED(128, 4, 4, 1, 2);
-        if (n <= 4096) return HH_STAGED(256, 4, 4, 1, 2);
+        if (n <= 4096) return HH_STAGED(HH_N4096_G, HH_N4096_NG, HH_N4096_RT, HH_N4096_RG, HH_N4096_B);
         return HH_STAGED(512, 4, 2, 1, 2);
 #undef HH_STAGED
     }

@@ -96,6 +96,7 @@ struct SCfg {
     static constexpr int COVER = G * E;   // columns covered
     static constexpr int NV = B * RT;     // dot products reduced together
     static constexpr int L = 32 / NV;     // lanes holding one value after the warp reduction
+    static constexpr bool KEEP = B * E <= 32;  // keep the block's reflector values in registers
     static_assert(G % 32 == 0, "G must be a multiple of 32");
     static_assert(RG == 1 || NW == 1, "several row groups only with one warp each");
     static_assert(NV <= 32 && (NV & (NV - 1)) == 0, "B*RT must be a power of two <= 32");
@@ -136,28 +137,36 @@ __device__ __forceinline__ void chain(
             kk[j] = asc ? s + j : h - 1 - s - j;
             tk[j] = j < nb ? __ldg(tau + kk[j]) : 0.f;
         }
-        float2 u[B][E2];
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
+        // Reflector values: all B kept in registers between the dot and the
+        // update phase (KEEP), or one at a time and read again for the update.
+        constexpr int KB = C::KEEP ? B : 1;
+        float2 u[KB][E2];
+        auto load_u = [&](int j, float2(&dst)[E2]) {
 #pragma unroll
             for (int i = 0; i < NG; ++i) {
                 float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (j < nb)
                     q = __ldg(reinterpret_cast<const float4 *>(V + (size_t)kk[j] * ldv) + (t + G * i));
-                u[j][2 * i] = make_float2(q.x, q.y);
-                u[j][2 * i + 1] = make_float2(q.z, q.w);
+                dst[2 * i] = make_float2(q.x, q.y);
+                dst[2 * i + 1] = make_float2(q.z, q.w);
             }
+        };
+        if constexpr (C::KEEP) {
+#pragma unroll
+            for (int j = 0; j < B; ++j) load_u(j, u[j]);
         }
         float p[NV];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
+            if constexpr (!C::KEEP) load_u(j, u[0]);
+            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
                 float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int e = 0; e < E2; e += 2) {
-                    a = __ffma2_rn(x[r][e], u[j][e], a);
-                    if (e + 1 < E2) b = __ffma2_rn(x[r][e + 1], u[j][e + 1], b);
+                    a = __ffma2_rn(x[r][e], uj[e], a);
+                    if (e + 1 < E2) b = __ffma2_rn(x[r][e + 1], uj[e + 1], b);
                 }
                 a = __fadd2_rn(a, b);
                 p[j * RT + r] = a.x + a.y;
@@ -191,22 +200,27 @@ __device__ __forceinline__ void chain(
             for (int qq = 0; qq < NV; ++qq) z[qq] = __shfl_sync(0xffffffffu, q, qq * L);
             buf ^= 1;
         }
-        // coefficients in the order the reflectors act, then the update
+        // coefficients in the order the reflectors act (negated), then the update
+        float c[B][RT];
 #pragma unroll
         for (int r = 0; r < RT; ++r) {
-            float c[B];
 #pragma unroll
             for (int j = 0; j < B; ++j) {
                 float acc = z[j * RT + r];
 #pragma unroll
-                for (int i = 0; i < j; ++i) acc = fmaf(-c[i], gij[i][j], acc);
-                c[j] = tk[j] * acc;
+                for (int i = 0; i < j; ++i) acc = fmaf(c[i][r], gij[i][j], acc);
+                c[j][r] = -tk[j] * acc;
             }
+        }
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const float2 cc = make_float2(-c[j], -c[j]);
+        for (int j = 0; j < B; ++j) {
+            if constexpr (!C::KEEP) load_u(j, u[0]);
+            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
 #pragma unroll
-                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(u[j][e], cc, x[r][e]);
+            for (int r = 0; r < RT; ++r) {
+                const float2 cc = make_float2(c[j][r], c[j][r]);
+#pragma unroll
+                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
             }
         }
     }
