@@ -154,7 +154,7 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
     if ((e = cudaMalloc(&p->u, es * (size_t)p->ldv * (size_t)(h > 0 ? h : 1))) ||
         (e = cudaMalloc(&p->tau, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
         (e = cudaMalloc(&p->tau_t, es * (size_t)(h > 0 ? h : 1))) ||
-        (e = cudaMalloc(&p->gram, es * 4 * (size_t)(h > 0 ? h : 1))) ||
+        (e = cudaMalloc(&p->gram, es * 16 * (size_t)(h > 0 ? h : 1))) ||
         (e = cudaMalloc(&p->vnorm, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
         (d && (e = cudaMalloc(&p->d, es * (size_t)p->ldv))) ||
         (sign && (e = cudaMalloc(&p->sign, es * (size_t)p->ldv))) ||

@@ -35,7 +35,7 @@ struct Plan {
     // FUSED path, compute dtype (float or double):
     void *u = nullptr;      // h x ldv, v_k as given (zero padded), compute dtype
     void *tau_t = nullptr;  // h, tau_k rounded to the compute dtype: H_k z = z - tau_k v_k (v_k . z)
-    void *gram = nullptr;   // h x 4, gram[k*4 + j] = v_k . v_{k+j} (j = 1..3, FP64 sums), compute dtype
+    void *gram = nullptr;   // h x 16, gram[k*16 + j] = v_k . v_{k+j} (j = 1..15, FP64 sums), compute dtype
     void *d = nullptr;      // ldv, spectrum (zero padded), or null
     void *sign = nullptr;   // ldv, +-1 (one padded), or null
     double *tau = nullptr;  // h, tau_k = 2 / v_k^T v_k (0 for v_k = 0)

@@ -56,15 +56,15 @@ prepare_reflectors_kernel(const Tin *__restrict__ U, int64_t ldu, int64_t n, int
 }
 
 // Band of the reflector Gram matrix used by the blocked chain kernels:
-// gram[k*4 + j] = v_k . v_{k+j} for j = 1..3 (FP64 sum, fixed-order tree), 0
-// where k + j >= h; gram[k*4] is unused (0).  One CTA per (k, j).
+// gram[k*16 + j] = v_k . v_{k+j} for j = 1..15 (FP64 sum, fixed-order tree),
+// 0 where k + j >= h; gram[k*16] is unused (0).  One CTA per (k, j).
 template <typename T>
 __global__ void __launch_bounds__(kPrepThreads)
 prepare_gram_kernel(const T *__restrict__ u, int64_t ldv, int64_t n, int64_t h,
                     T *__restrict__ gram) {
     __shared__ double red[kPrepThreads];
     const int64_t k = blockIdx.x;
-    const int j = blockIdx.y;  // 0..3
+    const int j = blockIdx.y;  // 0..15
     double s = 0.0;
     if (j > 0 && k + j < h) {
         const T *a = u + k * ldv, *b = u + (k + j) * ldv;
@@ -76,7 +76,7 @@ prepare_gram_kernel(const T *__restrict__ u, int64_t ldv, int64_t n, int64_t h,
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gram[k * 4 + j] = (T)red[0];
+    if (threadIdx.x == 0) gram[k * 16 + j] = (T)red[0];
 }
 
 template <typename Tin, typename Tout>
@@ -104,7 +104,7 @@ hh_status prepare_typed(Plan *p, const void *U, int64_t ldu, const void *d, cons
     if (p->h > 0) {
         prepare_reflectors_kernel<T, T><<<(unsigned)p->h, kPrepThreads, 0, st>>>(
             (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, (T *)p->tau_t, p->vnorm, flag);
-        prepare_gram_kernel<T><<<dim3((unsigned)p->h, 4), kPrepThreads, 0, st>>>(
+        prepare_gram_kernel<T><<<dim3((unsigned)p->h, 16), kPrepThreads, 0, st>>>(
             (const T *)p->u, p->ldv, p->n, p->h, (T *)p->gram);
     }
     if (d || sign) {

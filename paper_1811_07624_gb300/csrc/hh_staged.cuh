@@ -33,7 +33,7 @@ namespace hh {
 namespace staged {
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
-constexpr int kGramBand = 4;                     // Gram entries stored per reflector
+constexpr int kGramBand = 16;                    // Gram entries stored per reflector
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -172,16 +172,6 @@ __device__ __forceinline__ void chain(
                 p[j * RT + r] = a.x + a.y;
             }
         }
-        // Gram entries of the block (uniform scalars; the smaller index of each
-        // pair addresses the band)
-        float gij[B][B];
-#pragma unroll
-        for (int i = 0; i < B; ++i)
-#pragma unroll
-            for (int j = i + 1; j < B; ++j) {
-                const int lo = asc ? kk[i] : kk[j];
-                gij[i][j] = j < nb ? __ldg(gram + (size_t)lo * kGramBand + (j - i)) : 0.f;
-            }
         float v = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
         float z[NV];
         if constexpr (NW == 1) {
@@ -200,16 +190,25 @@ __device__ __forceinline__ void chain(
             for (int qq = 0; qq < NV; ++qq) z[qq] = __shfl_sync(0xffffffffu, q, qq * L);
             buf ^= 1;
         }
-        // coefficients in the order the reflectors act (negated), then the update
+        // Coefficients in the order the reflectors act, stored negated:
+        // c_j = -tau_j (z_j - sum_{i<j} c_i g_ij), resolved left to right.  The
+        // Gram entries are uniform scalars read through L1 (the smaller index
+        // of each pair addresses the band).
         float c[B][RT];
 #pragma unroll
-        for (int r = 0; r < RT; ++r) {
+        for (int j = 0; j < B; ++j)
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                float acc = z[j * RT + r];
+            for (int r = 0; r < RT; ++r) c[j][r] = z[j * RT + r];
 #pragma unroll
-                for (int i = 0; i < j; ++i) acc = fmaf(c[i][r], gij[i][j], acc);
-                c[j][r] = -tk[j] * acc;
+        for (int j = 0; j < B; ++j) {
+#pragma unroll
+            for (int r = 0; r < RT; ++r) c[j][r] *= -tk[j];
+#pragma unroll
+            for (int i = j + 1; i < B; ++i) {
+                const int lo = asc ? kk[j] : kk[i];
+                const float g = i < nb ? __ldg(gram + (size_t)lo * kGramBand + (i - j)) : 0.f;
+#pragma unroll
+                for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], g, c[i][r]);
             }
         }
 #pragma unroll
