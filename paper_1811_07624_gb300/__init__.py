@@ -8,5 +8,7 @@ behind the C ABI of ``include/hh.h``.
 
 from ._lib import HHError, header_symbols, lib  # noqa: F401
 from .api import Plan  # noqa: F401
+from . import autograd  # noqa: F401
+from .autograd import ReflectorTransform  # noqa: F401
 
-__all__ = ["Plan", "HHError", "lib", "header_symbols"]
+__all__ = ["Plan", "HHError", "lib", "header_symbols", "autograd", "ReflectorTransform"]

@@ -136,3 +136,32 @@ class Plan:
 
     def apply_mode(self, mode: str, X, out=None, stream=None):
         return {"W": self.apply, "WT": self.apply_T, "SYM": self.apply_sym}[mode](X, out, stream)
+
+    # -- backward -----------------------------------------------------------------
+    def backward(self, mode: str, saved, gY, need_gX: bool = True, need_gU: bool = True,
+                 need_gd: bool | None = None, stream=None):
+        """Gradients of L with dL/dY = gY through ``apply_mode(mode, X)``.
+
+        saved: the forward output Y for modes "W" and "WT", the forward input X
+        for "SYM".  Returns (gX, gU, gd); gU (h, n) is the gradient with respect
+        to the reflector rows exactly as passed to the plan; gd (n,) only for SYM.
+        """
+        m = _lib.MODES[mode]
+        sp, lds = _rows(saved, "saved", self.n, self.dtype)
+        gp, ldg = _rows(gY, "gY", self.n, self.dtype)
+        if saved.shape[0] != gY.shape[0]:
+            raise ValueError("saved and gY must have the same number of rows")
+        B = saved.shape[0]
+        dev = saved.device
+        gX = torch.empty((B, self.n), device=dev, dtype=self.dtype) if need_gX else None
+        gU = torch.empty((self.h, self.n), device=dev, dtype=self.dtype) if need_gU and self.h else None
+        if need_gd is None:
+            need_gd = mode == "SYM"
+        gd = torch.empty((self.n,), device=dev, dtype=self.dtype) if need_gd and mode == "SYM" else None
+        xp, ldgx = (None, self.n) if gX is None else _rows(gX, "gX", self.n, self.dtype)
+        _lib.call("hh_backward", self._h, m, sp, lds, gp, ldg, xp, ldgx,
+                  None if gU is None else gU.data_ptr(), None if gd is None else gd.data_ptr(),
+                  B, _stream_ptr(stream))
+        if need_gU and self.h == 0:
+            gU = torch.zeros((0, self.n), device=dev, dtype=self.dtype)
+        return gX, gU, gd

@@ -1,0 +1,57 @@
+"""Differentiable reflector transforms on top of the plan API.
+
+``apply(X, U, d, sign, mode)`` is a ``torch.autograd.Function``: the forward
+runs the library's apply kernel, the backward its adjoint kernel
+(``hh_backward``), which recomputes the chain's intermediate vectors from the
+saved output (modes "W", "WT") or input ("SYM") instead of storing them.
+Gradients flow to X, to the reflector rows U (as given, unnormalised) and to
+the spectrum d.
+"""
+
+from __future__ import annotations
+
+import torch
+
+from .api import Plan
+
+
+class _ChainFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, U, d, plan, mode):
+        Y = plan.apply_mode(mode, X.contiguous())
+        ctx.plan = plan
+        ctx.mode = mode
+        ctx.save_for_backward(X if mode == "SYM" else Y)
+        return Y
+
+    @staticmethod
+    def backward(ctx, gY):
+        (saved,) = ctx.saved_tensors
+        need_x, need_u, need_d = ctx.needs_input_grad[:3]
+        gX, gU, gd = ctx.plan.backward(ctx.mode, saved, gY.contiguous(), need_gX=need_x,
+                                       need_gU=need_u, need_gd=need_d and ctx.mode == "SYM")
+        return gX, gU, gd, None, None
+
+
+def apply(X: torch.Tensor, U: torch.Tensor, d: torch.Tensor | None = None,
+          sign: torch.Tensor | None = None, mode: str = "W") -> torch.Tensor:
+    """Rows of X through sigma.*(W x) ("W"), W^T(sigma.*x) ("WT") or
+    sigma.*W(d.*W^T(sigma.*x)) ("SYM"), W = H_1...H_h with H_k from row k of U."""
+    plan = Plan(U.detach(), d=None if d is None else d.detach(), sign=sign)
+    return _ChainFunction.apply(X, U, d, plan, mode)
+
+
+class ReflectorTransform(torch.nn.Module):
+    """h learnable reflector vectors (rows of ``U``) and an optional learnable
+    spectrum ``d``; ``forward(X, mode)`` applies the chain to the rows of X."""
+
+    def __init__(self, n: int, h: int, spectrum: bool = True, sign: torch.Tensor | None = None,
+                 dtype=torch.float32, device="cuda", generator=None):
+        super().__init__()
+        U = torch.randn(h, n, dtype=dtype, device=device, generator=generator)
+        self.U = torch.nn.Parameter(U)
+        self.d = torch.nn.Parameter(torch.ones(n, dtype=dtype, device=device)) if spectrum else None
+        self.register_buffer("sign", None if sign is None else sign.to(device=device, dtype=torch.int8))
+
+    def forward(self, X: torch.Tensor, mode: str = "W") -> torch.Tensor:
+        return apply(X, self.U, self.d if mode == "SYM" else None, self.sign, mode)

@@ -93,6 +93,32 @@ static hh_status apply_common(hh_plan_t plan, hh_mode mode, const void *X, int64
     return fail(HH_ERR_UNSUPPORTED, "no kernel for this plan's path");
 }
 
+hh_status check_backward_args(const Plan *p, hh_mode mode, const void *saved, int64_t lds,
+                              const void *gY, int64_t ldgy, const void *gX, int64_t ldgx,
+                              const void *gU, const void *gd, int64_t batch) {
+    hh_status st = check_plan(p);
+    if (st) return st;
+    if (mode != HH_MODE_W && mode != HH_MODE_WT && mode != HH_MODE_SYM)
+        return fail(HH_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+    if (p->path != HH_PATH_FUSED)
+        return fail(HH_ERR_UNSUPPORTED, "backward: F32 and F64 plans only");
+    if (batch < 0) return fail(HH_ERR_INVALID_ARG, "batch %lld < 0", (long long)batch);
+    if (mode == HH_MODE_SYM && !p->d)
+        return fail(HH_ERR_INVALID_ARG, "backward SYM: the plan has no spectrum d");
+    if (gd && mode != HH_MODE_SYM)
+        return fail(HH_ERR_INVALID_ARG, "backward: gd is only defined for mode SYM");
+    if ((st = check_rows(p, saved, lds, batch, "saved"))) return st;
+    if ((st = check_rows(p, gY, ldgy, batch, "gY"))) return st;
+    if (gX && (st = check_rows(p, gX, ldgx, batch, "gX"))) return st;
+    if (gX && (gX == saved || gX == gY))
+        return fail(HH_ERR_INVALID_ARG, "backward: gX may not alias saved or gY");
+    if (gU && p->h > 0 && !device_ptr(gU, p->device))
+        return fail(HH_ERR_INVALID_ARG, "gU: not a device pointer of device %d", p->device);
+    if (gd && !device_ptr(gd, p->device))
+        return fail(HH_ERR_INVALID_ARG, "gd: not a device pointer of device %d", p->device);
+    return HH_OK;
+}
+
 }  // namespace hh
 
 using namespace hh;
@@ -251,9 +277,12 @@ hh_status hh_apply_sym(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int6
 hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t lds,
                       const void *gY, int64_t ldgy, void *gX, int64_t ldgx, void *gU, void *gd,
                       int64_t batch, void *stream) {
-    (void)plan; (void)mode; (void)saved; (void)lds; (void)gY; (void)ldgy; (void)gX; (void)ldgx;
-    (void)gU; (void)gd; (void)batch; (void)stream;
-    return fail(HH_ERR_UNSUPPORTED, "hh_backward is not built in this version");
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st = check_backward_args(p, mode, saved, lds, gY, ldgy, gX, ldgx, gU, gd, batch);
+    if (st) return st;
+    if (batch == 0 && !gU && !gd) return HH_OK;
+    return backward(p, mode, saved, lds, gY, ldgy, gX, ldgx, gU, gd, batch, nullptr, 0,
+                    reinterpret_cast<cudaStream_t>(stream));
 }
 
 hh_status hh_mahalanobis(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,

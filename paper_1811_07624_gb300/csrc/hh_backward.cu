@@ -1,0 +1,466 @@
+// Adjoint of the reflector chain (F32 / F64): gradients of a scalar loss L
+// with respect to the input vectors, the reflector vectors v_k and the
+// spectrum d, for the three forward modes of hh_fused.cuh.
+//
+// One reflector a_out = a_in - tau v (v . a_in), tau = 2 / (v . v) (§II-A,
+// Eq. (2)), with G = dL/da_out, has
+//     dL/da_in = H G = G - tau (v . G) v
+//     dL/dv    = tau (alpha G - beta a_in) - tau^2 alpha beta v,
+// where alpha = v . a_out = -(v . a_in) (since tau v.v = 2) and beta = v . G.
+// The kernel walks the chain from the output back to the input; it never
+// stores the intermediate vectors: a_in is recomputed from a_out by the
+// involution H H = I (§II-A), so modes W and W^T start from the saved forward
+// output.  Mode S (Eq. (21)) starts from the saved input, recomputes
+// p = W^T (sigma .* x) and W (d .* p) forwards, then walks back through both
+// halves (dL/dd = sum p .* dL/d(d .* p)).
+//
+// Reductions over the batch are deterministic: each CTA accumulates
+// P_k = sum (alpha G - beta a_in) over its rows (in shared memory when it
+// fits, else in its own slice of the scratch) and s_k = sum alpha beta, writes
+// its partials to the scratch, and a second kernel sums the partials in a
+// fixed order in FP64 and forms dL/dv_k = tau_k P_k - tau_k^2 s_k v_k.
+#include <algorithm>
+
+#include "hh_fused.cuh"
+
+namespace hh {
+namespace bwd {
+
+template <typename T, int G, int NG, int RT>
+struct BCfg {
+    static constexpr int VEC = fused::Granule<T>::N;
+    static constexpr int E = NG * VEC;
+    static constexpr int NW = G / 32;
+    static constexpr int COVER = G * E;
+    static constexpr int NV = 2 * RT;    // alpha and beta per row
+    static constexpr int L = 32 / NV;    // lanes per value after the warp reduction
+    static_assert(NV <= 32 && (NV & (NV - 1)) == 0, "2*RT must be a power of two <= 32");
+};
+
+template <typename T, int G, int NG, int RT>
+__device__ __forceinline__ void load_rows(T (&a)[RT][BCfg<T, G, NG, RT>::E], const T *A, int64_t lda,
+                                          int64_t r0, int64_t batch, int n, int t, int vec_ok) {
+    constexpr int VEC = BCfg<T, G, NG, RT>::VEC;
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const int64_t row = r0 + r;
+        const T *ar = A + row * lda;
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+            const int col = (t + G * i) * VEC;
+            T g[VEC];
+            if (row < batch && vec_ok && col + VEC <= n) {
+                fused::load_granule<T>(ar + col, g);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) g[e] = (row < batch && col + e < n) ? ar[col + e] : T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) a[r][i * VEC + e] = g[e];
+        }
+    }
+}
+
+template <typename T, int G, int NG, int RT>
+__device__ __forceinline__ void load_cols(T (&c)[BCfg<T, G, NG, RT>::E], const T *__restrict__ s,
+                                          int t) {
+    constexpr int VEC = BCfg<T, G, NG, RT>::VEC;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        T g[VEC];
+        fused::ldg_granule<T>(s + (size_t)(t + G * i) * VEC, g);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) c[i * VEC + e] = g[e];
+    }
+}
+
+// Sum NV per-thread values over the G threads of the CTA; every thread gets
+// all NV sums.  One CTA barrier (double-buffered shared partials).
+template <typename T, int G, int NG, int RT>
+__device__ __forceinline__ void cta_sum(T (&p)[BCfg<T, G, NG, RT>::NV], int lane, int warp,
+                                        T (*red)[BCfg<T, G, NG, RT>::NV][BCfg<T, G, NG, RT>::NW],
+                                        int &buf) {
+    using C = BCfg<T, G, NG, RT>;
+    constexpr int NV = C::NV, NW = C::NW, L = C::L;
+    T v = fused::warp_reduce_rows<T, NV>(p, lane);
+    if constexpr (NW == 1) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) p[q] = __shfl_sync(0xffffffffu, v, q * L);
+    } else {
+        if ((lane & (L - 1)) == 0) red[buf][lane / L][warp] = v;
+        __syncthreads();
+        const int idx = lane / L, sub = lane & (L - 1);
+        T q = T(0);
+        for (int w = sub; w < NW; w += L) q += red[buf][idx][w];
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+#pragma unroll
+        for (int qq = 0; qq < NV; ++qq) p[qq] = __shfl_sync(0xffffffffu, q, qq * L);
+        buf ^= 1;
+    }
+}
+
+// Forward reflector on the rows in a (used to recompute mode S's states).
+template <typename T, int G, int NG, int RT>
+__device__ __forceinline__ void forward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
+                                             const T (&v)[BCfg<T, G, NG, RT>::E], T tk, int lane,
+                                             int warp,
+                                             T (*red)[BCfg<T, G, NG, RT>::NV][BCfg<T, G, NG, RT>::NW],
+                                             int &buf) {
+    using C = BCfg<T, G, NG, RT>;
+    constexpr int E = C::E;
+    T p[C::NV];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        T s = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) s = fma(a[r][e], v[e], s);
+        p[r] = s;
+        p[RT + r] = T(0);
+    }
+    cta_sum<T, G, NG, RT>(p, lane, warp, red, buf);
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const T c = tk * p[r];
+#pragma unroll
+        for (int e = 0; e < E; ++e) a[r][e] = fma(-c, v[e], a[r][e]);
+    }
+}
+
+// One backward reflector step on (a = output of H_k, g = dL/d output).
+// Leaves a = input of H_k, g = dL/d input; adds to the CTA's P_k accumulator
+// (this thread's columns) and, on thread 0, to s_k.
+template <typename T, int G, int NG, int RT>
+__device__ __forceinline__ void backward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
+                                              T (&g)[RT][BCfg<T, G, NG, RT>::E],
+                                              const T (&v)[BCfg<T, G, NG, RT>::E], T tk,
+                                              T *__restrict__ pk, double *sk, int t, int lane,
+                                              int warp,
+                                              T (*red)[BCfg<T, G, NG, RT>::NV][BCfg<T, G, NG, RT>::NW],
+                                              int &buf) {
+    using C = BCfg<T, G, NG, RT>;
+    constexpr int E = C::E, VEC = C::VEC;
+    T p[C::NV];
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        T sa = 0, sg = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            sa = fma(a[r][e], v[e], sa);
+            sg = fma(g[r][e], v[e], sg);
+        }
+        p[r] = sa;
+        p[RT + r] = sg;
+    }
+    cta_sum<T, G, NG, RT>(p, lane, warp, red, buf);
+    T acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = T(0);
+    double ab = 0.0;
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const T alpha = p[r], beta = p[RT + r];
+        const T ca = tk * alpha, cb = tk * beta;
+        ab += (double)alpha * (double)beta;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            a[r][e] = fma(-ca, v[e], a[r][e]);                        // a_in
+            acc[e] = fma(alpha, g[r][e], fma(-beta, a[r][e], acc[e]));  // alpha G - beta a_in
+            g[r][e] = fma(-cb, v[e], g[r][e]);                        // H G
+        }
+    }
+    if (threadIdx.x == 0) *sk += ab;
+#pragma unroll
+    for (int i = 0; i < NG; ++i)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) pk[(size_t)(t + G * i) * VEC + e] += acc[i * VEC + e];
+}
+
+// Grid-persistent backward.  part: per CTA (h + 1) rows of COVER values
+// (rows k < h: P_k; row h: the dL/dd partial), spart: per CTA h doubles (s_k).
+// With SMEM the accumulators live in shared memory and are copied to `part`
+// at the end; otherwise they are updated in place in `part`.
+template <typename T, int MODE, int G, int NG, int RT, bool SMEM>
+__global__ void __launch_bounds__(G)
+backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_t ldgx,
+                int64_t batch, int n, const T *__restrict__ V, const T *__restrict__ tau,
+                int64_t ldv, int h, const T *__restrict__ sign, const T *__restrict__ d,
+                T *__restrict__ part, double *__restrict__ spart, int vec_ok) {
+    using C = BCfg<T, G, NG, RT>;
+    constexpr int E = C::E, VEC = C::VEC, COVER = C::COVER;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[2][C::NV][C::NW];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    T *accp = SMEM ? reinterpret_cast<T *>(smem_raw) : part + (size_t)blockIdx.x * (h + 1) * COVER;
+    double *sacc = spart + (size_t)blockIdx.x * h;
+    // zero this thread's accumulator columns (same thread reads and writes them)
+    for (int k = 0; k <= h; ++k)
+#pragma unroll
+        for (int i = 0; i < NG; ++i)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) accp[(size_t)k * COVER + (size_t)(t + G * i) * VEC + e] = T(0);
+    if (t == 0)
+        for (int k = 0; k < h; ++k) sacc[k] = 0.0;
+    int buf = 0;
+    const int64_t tiles = (batch + RT - 1) / RT;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t r0 = tile * RT;
+        T a[RT][E], g[RT][E], v[E];
+        T sg[E];
+        if (sign) load_cols<T, G, NG, RT>(sg, sign, t);
+        load_rows<T, G, NG, RT>(g, gY, ldg, r0, batch, n, t, vec_ok);
+        T pvec[MODE == HH_MODE_SYM ? RT : 1][MODE == HH_MODE_SYM ? E : 1];
+        if (MODE == HH_MODE_SYM) {
+            // recompute p = W^T (sigma .* x), then W (d .* p)
+            load_rows<T, G, NG, RT>(a, S, lds, r0, batch, n, t, vec_ok);
+            if (sign)
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) a[r][e] *= sg[e];
+            for (int k = 0; k < h; ++k) {
+                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+                forward_step<T, G, NG, RT>(a, v, __ldg(tau + k), lane, warp, red, buf);
+            }
+            T dv[E];
+            load_cols<T, G, NG, RT>(dv, d, t);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if constexpr (MODE == HH_MODE_SYM) pvec[r][e] = a[r][e];
+                    a[r][e] *= dv[e];
+                }
+            for (int k = h - 1; k >= 0; --k) {
+                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+                forward_step<T, G, NG, RT>(a, v, __ldg(tau + k), lane, warp, red, buf);
+            }
+        } else {
+            load_rows<T, G, NG, RT>(a, S, lds, r0, batch, n, t, vec_ok);
+        }
+        // W part (modes W and S): y = sigma .* a^(1); walk k = 1..h
+        if (MODE != HH_MODE_WT) {
+            if (sign)
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        if (MODE == HH_MODE_W) a[r][e] *= sg[e];
+                        g[r][e] *= sg[e];
+                    }
+            for (int k = 0; k < h; ++k) {
+                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+                backward_step<T, G, NG, RT>(a, g, v, __ldg(tau + k), accp + (size_t)k * COVER,
+                                            sacc + k, t, lane, warp, red, buf);
+            }
+        }
+        if (MODE == HH_MODE_SYM) {
+            // dL/dd += p .* dL/dq;  dL/dp = d .* dL/dq; continue from a = p
+            T dv[E];
+            load_cols<T, G, NG, RT>(dv, d, t);
+            T dd[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) dd[e] = T(0);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if constexpr (MODE == HH_MODE_SYM) {
+                        dd[e] = fma(pvec[r][e], g[r][e], dd[e]);
+                        a[r][e] = pvec[r][e];
+                    }
+                    g[r][e] *= dv[e];
+                }
+            T *dk = accp + (size_t)h * COVER;
+#pragma unroll
+            for (int i = 0; i < NG; ++i)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) dk[(size_t)(t + G * i) * VEC + e] += dd[i * VEC + e];
+        }
+        // W^T part (modes WT and S): walk k = h..1; then dL/dx = sigma .* g
+        if (MODE != HH_MODE_W) {
+            for (int k = h - 1; k >= 0; --k) {
+                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+                backward_step<T, G, NG, RT>(a, g, v, __ldg(tau + k), accp + (size_t)k * COVER,
+                                            sacc + k, t, lane, warp, red, buf);
+            }
+            if (sign)
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) g[r][e] *= sg[e];
+        }
+        if (gX) {
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const int64_t row = r0 + r;
+                if (row >= batch) continue;
+                T *gr = gX + row * ldgx;
+#pragma unroll
+                for (int i = 0; i < NG; ++i) {
+                    const int col = (t + G * i) * VEC;
+                    T q[VEC];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) q[e] = g[r][i * VEC + e];
+                    if (vec_ok && col + VEC <= n) {
+                        fused::store_granule<T>(gr + col, q);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (col + e < n) gr[col + e] = q[e];
+                    }
+                }
+            }
+        }
+    }
+    if (SMEM) {
+        T *dst = part + (size_t)blockIdx.x * (h + 1) * COVER;
+        for (int k = 0; k <= h; ++k)
+#pragma unroll
+            for (int i = 0; i < NG; ++i)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const size_t o = (size_t)k * COVER + (size_t)(t + G * i) * VEC + e;
+                    dst[o] = accp[o];
+                }
+    }
+}
+
+// Fixed-order FP64 reduction of the partials.  Block k < h writes dL/dv_k
+// (gU row k, length n); block h writes dL/dd.
+template <typename T>
+__global__ void __launch_bounds__(256)
+reduce_kernel(const T *__restrict__ part, const double *__restrict__ spart, int nparts, int cover,
+              int n, int h, const T *__restrict__ V, int64_t ldv, const double *__restrict__ tau,
+              T *gU, T *gd) {
+    const int k = blockIdx.x;
+    if (k < h && !gU) return;
+    if (k == h && !gd) return;
+    double s = 0.0, t = 0.0;
+    if (k < h) {
+        for (int p = 0; p < nparts; ++p) s += spart[(size_t)p * h + k];
+        t = tau[k];
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double acc = 0.0;
+        for (int p = 0; p < nparts; ++p) acc += (double)part[((size_t)p * (h + 1) + k) * cover + j];
+        if (k < h)
+            gU[(size_t)k * n + j] = (T)(t * acc - t * t * s * (double)V[(size_t)k * ldv + j]);
+        else
+            gd[j] = (T)acc;
+    }
+}
+
+template <typename T, int G, int NG, int RT>
+hh_status run(const Plan *p, hh_mode mode, const T *S, int64_t lds, const T *gY, int64_t ldg,
+              T *gX, int64_t ldgx, T *gU, T *gd, int64_t batch, int vec_ok, void *scratch,
+              size_t scratch_bytes, cudaStream_t st) {
+    using C = BCfg<T, G, NG, RT>;
+    const int h = (int)p->h, n = (int)p->n;
+    const size_t acc_bytes = (size_t)(h + 1) * C::COVER * sizeof(T);
+    const bool use_smem = acc_bytes <= 48 * 1024;
+    auto pick = [&](auto kern, size_t smem) -> int {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, G, smem) != cudaSuccess || nb < 1)
+            nb = 1;
+        return nb;
+    };
+    const int64_t tiles = (batch + RT - 1) / RT;
+    auto launch = [&](auto kern, size_t smem) -> hh_status {
+        int nparts = (int)std::min<int64_t>(tiles, (int64_t)p->num_sms * pick(kern, smem));
+        if (nparts < 1) nparts = 1;
+        const size_t need = (size_t)nparts * (acc_bytes + (size_t)h * sizeof(double));
+        void *buf = scratch;
+        bool own = false;
+        if (!buf) {
+            cudaError_t e = cudaMallocAsync(&buf, need, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (backward scratch)");
+            own = true;
+        } else if (need > scratch_bytes) {
+            // fewer CTAs, each covering more rows, so the partials fit
+            const size_t per = acc_bytes + (size_t)h * sizeof(double);
+            nparts = (int)(scratch_bytes / per);
+            if (nparts < 1)
+                return fail(HH_ERR_INVALID_ARG,
+                            "scratch too small: %zu bytes, one CTA's partials need %zu",
+                            scratch_bytes, per);
+        }
+        T *part = reinterpret_cast<T *>(buf);
+        double *spart = reinterpret_cast<double *>(reinterpret_cast<char *>(buf) +
+                                                   (size_t)nparts * acc_bytes);
+        kern<<<nparts, G, smem, st>>>(S, lds, gY, ldg, gX, ldgx, batch, n, (const T *)p->u,
+                                      (const T *)p->tau_t, p->ldv, h, (const T *)p->sign,
+                                      (const T *)p->d, part, spart, vec_ok);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && (gU || gd))
+            reduce_kernel<T><<<h + 1, 256, 0, st>>>(part, spart, nparts, C::COVER, n, h,
+                                                    (const T *)p->u, p->ldv, p->tau, gU, gd);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (own) {
+            cudaError_t e2 = cudaFreeAsync(buf, st);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+        return HH_OK;
+    };
+#define HH_BWD_MODE(M)                                                  \
+    if (use_smem) {                                                     \
+        return launch(backward_kernel<T, M, G, NG, RT, true>, acc_bytes); \
+    } else {                                                            \
+        return launch(backward_kernel<T, M, G, NG, RT, false>, 0);      \
+    }
+    switch (mode) {
+        case HH_MODE_W: HH_BWD_MODE(HH_MODE_W)
+        case HH_MODE_WT: HH_BWD_MODE(HH_MODE_WT)
+        default: HH_BWD_MODE(HH_MODE_SYM)
+    }
+#undef HH_BWD_MODE
+}
+
+template <typename T>
+hh_status dispatch(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
+                   int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
+                   void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    const int64_t n = p->n;
+    const int vec = 16 / (int)sizeof(T);
+    const int vec_ok = ((uintptr_t)S % 16 == 0) && ((uintptr_t)gY % 16 == 0) &&
+                       (!gX || (uintptr_t)gX % 16 == 0) && lds % vec == 0 && ldg % vec == 0 &&
+                       (!gX || ldgx % vec == 0);
+#define HH_RUN(G, NG, RT)                                                                   \
+    return run<T, G, NG, RT>(p, mode, (const T *)S, lds, (const T *)gY, ldg, (T *)gX, ldgx, \
+                             (T *)gU, (T *)gd, batch, vec_ok, scratch, scratch_bytes, st)
+    if (sizeof(T) == 4) {
+        if (n <= 128) HH_RUN(32, 1, 4);
+        if (n <= 256) HH_RUN(32, 2, 2);
+        if (n <= 512) HH_RUN(64, 2, 2);
+        if (n <= 1024) HH_RUN(128, 2, 2);
+        if (n <= 2048) HH_RUN(256, 2, 2);
+        if (n <= 4096) HH_RUN(512, 2, 2);
+    } else {
+        if (n <= 64) HH_RUN(32, 1, 4);
+        if (n <= 128) HH_RUN(32, 2, 2);
+        if (n <= 256) HH_RUN(64, 2, 2);
+        if (n <= 512) HH_RUN(128, 2, 2);
+        if (n <= 1024) HH_RUN(256, 2, 2);
+        if (n <= 2048) HH_RUN(512, 2, 2);
+    }
+#undef HH_RUN
+    return fail(HH_ERR_UNSUPPORTED, "backward: n = %lld is above this build's limit (%d)",
+                (long long)n, sizeof(T) == 4 ? 4096 : 2048);
+}
+
+}  // namespace bwd
+
+hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
+                   int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
+                   void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    if (p->dtype == HH_F32)
+        return bwd::dispatch<float>(p, mode, S, lds, gY, ldg, gX, ldgx, gU, gd, batch, scratch,
+                                    scratch_bytes, st);
+    if (p->dtype == HH_F64)
+        return bwd::dispatch<double>(p, mode, S, lds, gY, ldg, gX, ldgx, gU, gd, batch, scratch,
+                                     scratch_bytes, st);
+    return fail(HH_ERR_UNSUPPORTED, "backward: F32 and F64 plans only");
+}
+
+}  // namespace hh

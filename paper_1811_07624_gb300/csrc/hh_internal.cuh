@@ -64,4 +64,11 @@ hh_status prepare_fused(Plan *p, const void *U, int64_t ldu, const void *d, cons
 hh_status fused_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void *Y,
                       int64_t ldy, int64_t batch, cudaStream_t st);
 
+// ---- adjoint (hh_backward.cu) ----
+// scratch: caller-provided device buffer of scratch_bytes, or null to allocate
+// (stream-ordered) per call.
+hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
+                   int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
+                   void *scratch, size_t scratch_bytes, cudaStream_t st);
+
 }  // namespace hh
