@@ -144,6 +144,33 @@ hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t l
                       void *gd, int64_t batch, void *stream);
 
 /*
+ * hh_backward that allocates nothing.  The paper has no counterpart: this
+ * entry point is for callers that cannot let a library allocate device memory
+ * on its own schedule, such as code running inside a host (a framework, a
+ * serving process, a plugin) that owns all of the device's memory and does
+ * not allow cudaMalloc behind its back, or a latency-bound training loop that
+ * must not block or fail with out-of-memory part-way through a step.
+ *
+ * Same arguments, results and errors as hh_backward, but its scratch is a
+ * fixed 32 MiB array that is part of the library's device image: every device
+ * that loads the library holds it until the process exits.  No cudaMalloc,
+ * cudaMallocAsync or cudaFree is called.  One CTA's partial sums take
+ * (h + 1) * C * s + 8 h bytes (s the element size, C the kernel's column tile:
+ * n rounded up to a power of two, at least 128 for F32 / 64 for F64); the call
+ * uses as many CTAs as fit and returns HH_ERR_INVALID_ARG when one does not
+ * (for example F32 with n = 4096 and h > 2046).
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array and the kernels initialise
+ * what they read, but calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on it and give wrong gradients: serialise them.
+ */
+hh_status hh_backward_noalloc(hh_plan_t plan, hh_mode mode, const void *saved, int64_t lds,
+                              const void *gY, int64_t ldgy, void *gX, int64_t ldgx, void *gU,
+                              void *gd, int64_t batch, void *stream);
+
+/*
  * Fast Mahalanobis distances (§IV-C): for p < npairs,
  *   out[p] = (x_a - x_b)^T S (x_a - x_b) = sum_m d_m [W^T (sigma .* (x_a - x_b))]_m^2
  * with x_a = row ia[p] and x_b = row ib[p] of X (int64 device indices, each

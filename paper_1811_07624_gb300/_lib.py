@@ -57,6 +57,7 @@ SIGNATURES = {
     "hh_apply_T": [vp, vp, i64, vp, i64, i64, vp],
     "hh_apply_sym": [vp, vp, i64, vp, i64, i64, vp],
     "hh_backward": [vp, ip, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
+    "hh_backward_noalloc": [vp, ip, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
     "hh_mahalanobis": [vp, vp, i64, i64, vp, vp, i64, vp, vp],
 }
 

@@ -382,8 +382,9 @@ hh_status run(const Plan *p, hh_mode mode, const T *S, int64_t lds, const T *gY,
             nparts = (int)(scratch_bytes / per);
             if (nparts < 1)
                 return fail(HH_ERR_INVALID_ARG,
-                            "scratch too small: %zu bytes, one CTA's partials need %zu",
-                            scratch_bytes, per);
+                            "backward: one CTA's partial sums need %zu bytes of scratch, more "
+                            "than the %zu bytes available (h or n too large)",
+                            per, scratch_bytes);
         }
         T *part = reinterpret_cast<T *>(buf);
         double *spart = reinterpret_cast<double *>(reinterpret_cast<char *>(buf) +

@@ -65,6 +65,10 @@ hh_status fused_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, v
                       int64_t ldy, int64_t batch, cudaStream_t st);
 
 // ---- adjoint (hh_backward.cu) ----
+// Argument checks shared by the adjoint entry points (hh_api.cu).
+hh_status check_backward_args(const Plan *p, hh_mode mode, const void *saved, int64_t lds,
+                              const void *gY, int64_t ldgy, const void *gX, int64_t ldgx,
+                              const void *gU, const void *gd, int64_t batch);
 // scratch: caller-provided device buffer of scratch_bytes, or null to allocate
 // (stream-ordered) per call.
 hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
