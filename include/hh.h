@@ -175,10 +175,25 @@ hh_status hh_backward_noalloc(hh_plan_t plan, hh_mode mode, const void *saved, i
  *   out[p] = (x_a - x_b)^T S (x_a - x_b) = sum_m d_m [W^T (sigma .* (x_a - x_b))]_m^2
  * with x_a = row ia[p] and x_b = row ib[p] of X (int64 device indices, each
  * in [0, nrows)).  out: npairs elements of the plan's dtype.  Needs d.
+ * F32 and F64 plans, n <= 4096.  An index outside [0, nrows) gives NaN for
+ * that pair and makes hh_sync report HH_ERR_INVALID_ARG.
  */
 hh_status hh_mahalanobis(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
                          const int64_t *ia, const int64_t *ib, int64_t npairs, void *out,
                          void *stream);
+
+/*
+ * Gradients of L = sum_p gout[p] * out[p] for the distances of hh_mahalanobis
+ * (a metric-learning loss, §IV-C): gU (h rows of n, with respect to the
+ * reflector vectors as given) and gd (n), each summed over the pairs, or NULL
+ * to skip.  gout: npairs device elements of the plan's dtype (dL/d out[p]).
+ * No gradient for X.  An index outside [0, nrows) contributes nothing and
+ * makes hh_sync report HH_ERR_INVALID_ARG.  Scratch is allocated per call
+ * with cudaMallocAsync on `stream`.
+ */
+hh_status hh_mahalanobis_backward(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
+                                  const int64_t *ia, const int64_t *ib, int64_t npairs,
+                                  const void *gout, void *gU, void *gd, void *stream);
 
 /* Message for the last failed call on this host thread ("" if none). */
 const char *hh_last_error(void);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "hh_backward": [vp, ip, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
     "hh_backward_noalloc": [vp, ip, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
     "hh_mahalanobis": [vp, vp, i64, i64, vp, vp, i64, vp, vp],
+    "hh_mahalanobis_backward": [vp, vp, i64, i64, vp, vp, i64, vp, vp, vp, vp],
 }
 
 

@@ -165,3 +165,34 @@ class Plan:
         if need_gU and self.h == 0:
             gU = torch.zeros((0, self.n), device=dev, dtype=self.dtype)
         return gX, gU, gd
+
+    # -- fast Mahalanobis distance (§IV-C) ------------------------------------------
+    def mahalanobis(self, X, ia, ib, out=None, stream=None):
+        """d_S(x_ia[p], x_ib[p]) = sum_m d_m [W^T(sigma.*(x_a - x_b))]_m^2 for each pair."""
+        xp, ldx = _rows(X, "X", self.n, self.dtype)
+        ia = ia.to(device=X.device, dtype=torch.int64).contiguous()
+        ib = ib.to(device=X.device, dtype=torch.int64).contiguous()
+        if ia.shape != ib.shape or ia.dim() != 1:
+            raise ValueError("ia, ib must be equal-length 1-D index tensors")
+        P = ia.shape[0]
+        if out is None:
+            out = torch.empty((P,), device=X.device, dtype=self.dtype)
+        _lib.call("hh_mahalanobis", self._h, xp, ldx, X.shape[0], ia.data_ptr(), ib.data_ptr(),
+                  P, out.data_ptr(), _stream_ptr(stream))
+        return out
+
+    def mahalanobis_backward(self, X, ia, ib, gout, need_gU=True, need_gd=True, stream=None):
+        """(gU, gd) of L = sum_p gout[p] d_S(x_ia[p], x_ib[p])."""
+        xp, ldx = _rows(X, "X", self.n, self.dtype)
+        ia = ia.to(device=X.device, dtype=torch.int64).contiguous()
+        ib = ib.to(device=X.device, dtype=torch.int64).contiguous()
+        gout = gout.to(device=X.device, dtype=self.dtype).contiguous()
+        gU = torch.empty((self.h, self.n), device=X.device, dtype=self.dtype) if need_gU and self.h else None
+        gd = torch.empty((self.n,), device=X.device, dtype=self.dtype) if need_gd else None
+        _lib.call("hh_mahalanobis_backward", self._h, xp, ldx, X.shape[0], ia.data_ptr(),
+                  ib.data_ptr(), ia.shape[0], gout.data_ptr(),
+                  None if gU is None else gU.data_ptr(), None if gd is None else gd.data_ptr(),
+                  _stream_ptr(stream))
+        if need_gU and self.h == 0:
+            gU = torch.zeros((0, self.n), device=X.device, dtype=self.dtype)
+        return gU, gd

@@ -41,6 +41,31 @@ def apply(X: torch.Tensor, U: torch.Tensor, d: torch.Tensor | None = None,
     return _ChainFunction.apply(X, U, d, plan, mode)
 
 
+class _MahalanobisFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, U, d, plan, ia, ib):
+        out = plan.mahalanobis(X.contiguous(), ia, ib)
+        ctx.plan = plan
+        ctx.save_for_backward(X, ia, ib)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        X, ia, ib = ctx.saved_tensors
+        gU, gd = ctx.plan.mahalanobis_backward(X.contiguous(), ia, ib, gout.contiguous(),
+                                               need_gU=ctx.needs_input_grad[1],
+                                               need_gd=ctx.needs_input_grad[2])
+        return None, gU, gd, None, None, None
+
+
+def mahalanobis(X: torch.Tensor, ia: torch.Tensor, ib: torch.Tensor, U: torch.Tensor,
+                d: torch.Tensor, sign: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable fast Mahalanobis distances of the row pairs (ia[p], ib[p]) of X,
+    with gradients for U and d (§IV-C)."""
+    plan = Plan(U.detach(), d=d.detach(), sign=sign)
+    return _MahalanobisFunction.apply(X, U, d, plan, ia, ib)
+
+
 class ReflectorTransform(torch.nn.Module):
     """h learnable reflector vectors (rows of ``U``) and an optional learnable
     spectrum ``d``; ``forward(X, mode)`` applies the chain to the rows of X."""

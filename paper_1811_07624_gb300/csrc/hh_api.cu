@@ -245,6 +245,8 @@ hh_status hh_sync(hh_plan_t plan, void *stream) {
         return cuda_fail(e, "hh_sync");
     if (word == HH_ERR_TIMEOUT)
         return fail(HH_ERR_TIMEOUT, "a kernel's bounded wait on its bulk copy expired");
+    if (word == HH_ERR_INVALID_ARG)
+        return fail(HH_ERR_INVALID_ARG, "a pair index was outside [0, nrows)");
     if (word != 0) return fail(HH_ERR_CUDA, "device status word %d", word);
     return HH_OK;
 }
@@ -285,12 +287,51 @@ hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t l
                     reinterpret_cast<cudaStream_t>(stream));
 }
 
+static hh_status check_pairs(const Plan *p, const void *X, int64_t ldx, int64_t nrows,
+                             const int64_t *ia, const int64_t *ib, int64_t npairs) {
+    hh_status st = check_plan(p);
+    if (st) return st;
+    if (p->path != HH_PATH_FUSED)
+        return fail(HH_ERR_UNSUPPORTED, "mahalanobis: F32 and F64 plans only");
+    if (!p->d) return fail(HH_ERR_INVALID_ARG, "mahalanobis: the plan has no spectrum d");
+    if (nrows < 0 || npairs < 0)
+        return fail(HH_ERR_INVALID_ARG, "nrows = %lld, npairs = %lld", (long long)nrows,
+                    (long long)npairs);
+    if (npairs > 0 && nrows == 0) return fail(HH_ERR_INVALID_ARG, "pairs given but X has no rows");
+    if ((st = check_rows(p, X, ldx, npairs > 0 ? nrows : 0, "X"))) return st;
+    if (npairs > 0 && (!device_ptr(ia, p->device) || !device_ptr(ib, p->device)))
+        return fail(HH_ERR_INVALID_ARG, "ia, ib: not device pointers of device %d", p->device);
+    return HH_OK;
+}
+
 hh_status hh_mahalanobis(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
                          const int64_t *ia, const int64_t *ib, int64_t npairs, void *out,
                          void *stream) {
-    (void)plan; (void)X; (void)ldx; (void)nrows; (void)ia; (void)ib; (void)npairs; (void)out;
-    (void)stream;
-    return fail(HH_ERR_UNSUPPORTED, "hh_mahalanobis is not built in this version");
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st = check_pairs(p, X, ldx, nrows, ia, ib, npairs);
+    if (st) return st;
+    if (npairs == 0) return HH_OK;
+    if (!device_ptr(out, p->device))
+        return fail(HH_ERR_INVALID_ARG, "out: not a device pointer of device %d", p->device);
+    return mahalanobis(p, X, ldx, nrows, ia, ib, npairs, out,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+hh_status hh_mahalanobis_backward(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
+                                  const int64_t *ia, const int64_t *ib, int64_t npairs,
+                                  const void *gout, void *gU, void *gd, void *stream) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st = check_pairs(p, X, ldx, nrows, ia, ib, npairs);
+    if (st) return st;
+    if (npairs > 0 && !device_ptr(gout, p->device))
+        return fail(HH_ERR_INVALID_ARG, "gout: not a device pointer of device %d", p->device);
+    if (gU && p->h > 0 && !device_ptr(gU, p->device))
+        return fail(HH_ERR_INVALID_ARG, "gU: not a device pointer of device %d", p->device);
+    if (gd && !device_ptr(gd, p->device))
+        return fail(HH_ERR_INVALID_ARG, "gd: not a device pointer of device %d", p->device);
+    if (!gU && !gd) return HH_OK;
+    return mahalanobis_backward(p, X, ldx, nrows, ia, ib, npairs, gout, gU, gd,
+                                reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -14,6 +14,11 @@
 // p = W^T (sigma .* x) and W (d .* p) forwards, then walks back through both
 // halves (dL/dd = sum p .* dL/d(d .* p)).
 //
+// Mode 3 is the fast Mahalanobis distance of §IV-C, d_p = sum_m d_m z_m^2 with
+// z = W^T (sigma .* (x_a - x_b)) for gathered row pairs: given g_p = dL/dd_p it
+// recomputes z, seeds dL/dz = 2 g_p d .* z, adds g_p z .* z to dL/dd and walks
+// back through W^T (no gradient for X).
+//
 // Reductions over the batch are deterministic: each CTA accumulates
 // P_k = sum (alpha G - beta a_in) over its rows (in shared memory when it
 // fits, else in its own slice of the scratch) and s_k = sum alpha beta, writes
@@ -180,12 +185,62 @@ __device__ __forceinline__ void backward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
 // (rows k < h: P_k; row h: the dL/dd partial), spart: per CTA h doubles (s_k).
 // With SMEM the accumulators live in shared memory and are copied to `part`
 // at the end; otherwise they are updated in place in `part`.
+constexpr int kModeMahalanobis = 3;
+
+// Rows x_ia[p] - x_ib[p] for the RT pairs of a tile (zero for pairs past the
+// end; an index outside [0, nrows) gives a zero row and sets *err).
+template <typename T, int G, int NG, int RT>
+__device__ __forceinline__ void load_pair_rows(T (&a)[RT][BCfg<T, G, NG, RT>::E], const T *X,
+                                               int64_t ldx, int64_t nrows,
+                                               const int64_t *__restrict__ ia,
+                                               const int64_t *__restrict__ ib, int64_t r0,
+                                               int64_t npairs, int n, int t, int vec_ok,
+                                               int *err) {
+    constexpr int VEC = BCfg<T, G, NG, RT>::VEC;
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const int64_t pr = r0 + r;
+        int64_t ra = 0, rb = 0;
+        bool live = pr < npairs;
+        if (live) {
+            ra = ia[pr];
+            rb = ib[pr];
+            if (ra < 0 || ra >= nrows || rb < 0 || rb >= nrows) {
+                live = false;
+                ra = rb = 0;
+                if (t == 0) atomicExch(err, (int)HH_ERR_INVALID_ARG);
+            }
+        }
+        const T *xa = X + ra * ldx, *xb = X + rb * ldx;
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+            const int col = (t + G * i) * VEC;
+            T ga[VEC], gb[VEC];
+            if (live && vec_ok && col + VEC <= n) {
+                fused::ldg_granule<T>(xa + col, ga);
+                fused::ldg_granule<T>(xb + col, gb);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const bool in = live && col + e < n;
+                    ga[e] = in ? xa[col + e] : T(0);
+                    gb[e] = in ? xb[col + e] : T(0);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) a[r][i * VEC + e] = ga[e] - gb[e];
+        }
+    }
+}
+
 template <typename T, int MODE, int G, int NG, int RT, bool SMEM>
 __global__ void __launch_bounds__(G)
 backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_t ldgx,
                 int64_t batch, int n, const T *__restrict__ V, const T *__restrict__ tau,
                 int64_t ldv, int h, const T *__restrict__ sign, const T *__restrict__ d,
-                T *__restrict__ part, double *__restrict__ spart, int vec_ok) {
+                T *__restrict__ part, double *__restrict__ spart, int vec_ok,
+                const int64_t *__restrict__ ia, const int64_t *__restrict__ ib, int64_t nrows,
+                int *__restrict__ err) {
     using C = BCfg<T, G, NG, RT>;
     constexpr int E = C::E, VEC = C::VEC, COVER = C::COVER;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -208,6 +263,43 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
         T a[RT][E], g[RT][E], v[E];
         T sg[E];
         if (sign) load_cols<T, G, NG, RT>(sg, sign, t);
+        if constexpr (MODE == kModeMahalanobis) {
+            // z = W^T (sigma .* (x_a - x_b)); dL/dz = 2 g_p d .* z; dL/dd += g_p z .* z
+            load_pair_rows<T, G, NG, RT>(a, S, lds, nrows, ia, ib, r0, batch, n, t, vec_ok, err);
+            if (sign)
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) a[r][e] *= sg[e];
+            for (int k = 0; k < h; ++k) {
+                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+                forward_step<T, G, NG, RT>(a, v, __ldg(tau + k), lane, warp, red, buf);
+            }
+            T dv[E], dd[E];
+            load_cols<T, G, NG, RT>(dv, d, t);
+#pragma unroll
+            for (int e = 0; e < E; ++e) dd[e] = T(0);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const T gp = r0 + r < batch ? gY[r0 + r] : T(0);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    dd[e] = fma(gp * a[r][e], a[r][e], dd[e]);
+                    g[r][e] = T(2) * gp * dv[e] * a[r][e];
+                }
+            }
+            T *dk = accp + (size_t)h * COVER;
+#pragma unroll
+            for (int i = 0; i < NG; ++i)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) dk[(size_t)(t + G * i) * VEC + e] += dd[i * VEC + e];
+            for (int k = h - 1; k >= 0; --k) {
+                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+                backward_step<T, G, NG, RT>(a, g, v, __ldg(tau + k), accp + (size_t)k * COVER,
+                                            sacc + k, t, lane, warp, red, buf);
+            }
+            continue;
+        }
         load_rows<T, G, NG, RT>(g, gY, ldg, r0, batch, n, t, vec_ok);
         T pvec[MODE == HH_MODE_SYM ? RT : 1][MODE == HH_MODE_SYM ? E : 1];
         if (MODE == HH_MODE_SYM) {
@@ -351,10 +443,15 @@ reduce_kernel(const T *__restrict__ part, const double *__restrict__ spart, int 
     }
 }
 
+struct PairArgs {
+    const int64_t *ia = nullptr, *ib = nullptr;
+    int64_t nrows = 0;
+};
+
 template <typename T, int G, int NG, int RT>
-hh_status run(const Plan *p, hh_mode mode, const T *S, int64_t lds, const T *gY, int64_t ldg,
+hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int64_t ldg,
               T *gX, int64_t ldgx, T *gU, T *gd, int64_t batch, int vec_ok, void *scratch,
-              size_t scratch_bytes, cudaStream_t st) {
+              size_t scratch_bytes, PairArgs pa, cudaStream_t st) {
     using C = BCfg<T, G, NG, RT>;
     const int h = (int)p->h, n = (int)p->n;
     const size_t acc_bytes = (size_t)(h + 1) * C::COVER * sizeof(T);
@@ -391,7 +488,8 @@ hh_status run(const Plan *p, hh_mode mode, const T *S, int64_t lds, const T *gY,
                                                    (size_t)nparts * acc_bytes);
         kern<<<nparts, G, smem, st>>>(S, lds, gY, ldg, gX, ldgx, batch, n, (const T *)p->u,
                                       (const T *)p->tau_t, p->ldv, h, (const T *)p->sign,
-                                      (const T *)p->d, part, spart, vec_ok);
+                                      (const T *)p->d, part, spart, vec_ok, pa.ia, pa.ib,
+                                      pa.nrows, p->err);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess && (gU || gd))
             reduce_kernel<T><<<h + 1, 256, 0, st>>>(part, spart, nparts, C::COVER, n, h,
@@ -413,23 +511,26 @@ hh_status run(const Plan *p, hh_mode mode, const T *S, int64_t lds, const T *gY,
     switch (mode) {
         case HH_MODE_W: HH_BWD_MODE(HH_MODE_W)
         case HH_MODE_WT: HH_BWD_MODE(HH_MODE_WT)
-        default: HH_BWD_MODE(HH_MODE_SYM)
+        case HH_MODE_SYM: HH_BWD_MODE(HH_MODE_SYM)
+        default: HH_BWD_MODE(kModeMahalanobis)
     }
 #undef HH_BWD_MODE
 }
 
 template <typename T>
-hh_status dispatch(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
+hh_status dispatch(const Plan *p, int mode, const void *S, int64_t lds, const void *gY,
                    int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
-                   void *scratch, size_t scratch_bytes, cudaStream_t st) {
+                   void *scratch, size_t scratch_bytes, PairArgs pa, cudaStream_t st) {
     const int64_t n = p->n;
     const int vec = 16 / (int)sizeof(T);
-    const int vec_ok = ((uintptr_t)S % 16 == 0) && ((uintptr_t)gY % 16 == 0) &&
-                       (!gX || (uintptr_t)gX % 16 == 0) && lds % vec == 0 && ldg % vec == 0 &&
-                       (!gX || ldgx % vec == 0);
+    // mode 3 reads gY as one value per pair: only S's alignment matters there
+    const int vec_ok = ((uintptr_t)S % 16 == 0) && lds % vec == 0 &&
+                       (mode == kModeMahalanobis ||
+                        ((uintptr_t)gY % 16 == 0 && ldg % vec == 0 &&
+                         (!gX || ((uintptr_t)gX % 16 == 0 && ldgx % vec == 0))));
 #define HH_RUN(G, NG, RT)                                                                   \
     return run<T, G, NG, RT>(p, mode, (const T *)S, lds, (const T *)gY, ldg, (T *)gX, ldgx, \
-                             (T *)gU, (T *)gd, batch, vec_ok, scratch, scratch_bytes, st)
+                             (T *)gU, (T *)gd, batch, vec_ok, scratch, scratch_bytes, pa, st)
     if (sizeof(T) == 4) {
         if (n <= 128) HH_RUN(32, 1, 4);
         if (n <= 256) HH_RUN(32, 2, 2);
@@ -455,13 +556,31 @@ hh_status dispatch(const Plan *p, hh_mode mode, const void *S, int64_t lds, cons
 hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
                    int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
                    void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    bwd::PairArgs pa;
     if (p->dtype == HH_F32)
         return bwd::dispatch<float>(p, mode, S, lds, gY, ldg, gX, ldgx, gU, gd, batch, scratch,
-                                    scratch_bytes, st);
+                                    scratch_bytes, pa, st);
     if (p->dtype == HH_F64)
         return bwd::dispatch<double>(p, mode, S, lds, gY, ldg, gX, ldgx, gU, gd, batch, scratch,
-                                     scratch_bytes, st);
+                                     scratch_bytes, pa, st);
     return fail(HH_ERR_UNSUPPORTED, "backward: F32 and F64 plans only");
+}
+
+hh_status mahalanobis_backward(const Plan *p, const void *X, int64_t ldx, int64_t nrows,
+                               const int64_t *ia, const int64_t *ib, int64_t npairs,
+                               const void *gout, void *gU, void *gd, cudaStream_t st) {
+    bwd::PairArgs pa;
+    pa.ia = ia;
+    pa.ib = ib;
+    pa.nrows = nrows;
+    const int m = bwd::kModeMahalanobis;
+    if (p->dtype == HH_F32)
+        return bwd::dispatch<float>(p, m, X, ldx, gout, 1, nullptr, p->n, gU, gd, npairs, nullptr,
+                                    0, pa, st);
+    if (p->dtype == HH_F64)
+        return bwd::dispatch<double>(p, m, X, ldx, gout, 1, nullptr, p->n, gU, gd, npairs, nullptr,
+                                     0, pa, st);
+    return fail(HH_ERR_UNSUPPORTED, "mahalanobis backward: F32 and F64 plans only");
 }
 
 }  // namespace hh

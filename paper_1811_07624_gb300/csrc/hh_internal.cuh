@@ -75,4 +75,11 @@ hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, cons
                    int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
                    void *scratch, size_t scratch_bytes, cudaStream_t st);
 
+// ---- fast Mahalanobis distance (hh_mahalanobis.cu, hh_backward.cu) ----
+hh_status mahalanobis(const Plan *p, const void *X, int64_t ldx, int64_t nrows, const int64_t *ia,
+                      const int64_t *ib, int64_t npairs, void *out, cudaStream_t st);
+hh_status mahalanobis_backward(const Plan *p, const void *X, int64_t ldx, int64_t nrows,
+                               const int64_t *ia, const int64_t *ib, int64_t npairs,
+                               const void *gout, void *gU, void *gd, cudaStream_t st);
+
 }  // namespace hh
