@@ -83,8 +83,7 @@ __device__ __forceinline__ void load_cols(T (&c)[BCfg<T, G, NG, RT>::E], const T
 // all NV sums.  One CTA barrier (double-buffered shared partials).
 template <typename T, int G, int NG, int RT>
 __device__ __forceinline__ void cta_sum(T (&p)[BCfg<T, G, NG, RT>::NV], int lane, int warp,
-                                        T (*red)[BCfg<T, G, NG, RT>::NV][BCfg<T, G, NG, RT>::NW],
-                                        int &buf) {
+                                        T *red, int &buf) {
     using C = BCfg<T, G, NG, RT>;
     constexpr int NV = C::NV, NW = C::NW, L = C::L;
     T v = fused::warp_reduce_rows<T, NV>(p, lane);
@@ -92,11 +91,11 @@ __device__ __forceinline__ void cta_sum(T (&p)[BCfg<T, G, NG, RT>::NV], int lane
 #pragma unroll
         for (int q = 0; q < NV; ++q) p[q] = __shfl_sync(0xffffffffu, v, q * L);
     } else {
-        if ((lane & (L - 1)) == 0) red[buf][lane / L][warp] = v;
+        if ((lane & (L - 1)) == 0) red[fused::red_index<1, NV, NW>(buf, 0, lane / L, warp)] = v;
         __syncthreads();
         const int idx = lane / L, sub = lane & (L - 1);
         T q = T(0);
-        for (int w = sub; w < NW; w += L) q += red[buf][idx][w];
+        for (int w = sub; w < NW; w += L) q += red[fused::red_index<1, NV, NW>(buf, 0, idx, w)];
 #pragma unroll
         for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
 #pragma unroll
@@ -109,9 +108,7 @@ __device__ __forceinline__ void cta_sum(T (&p)[BCfg<T, G, NG, RT>::NV], int lane
 template <typename T, int G, int NG, int RT>
 __device__ __forceinline__ void forward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
                                              const T (&v)[BCfg<T, G, NG, RT>::E], T tk, int lane,
-                                             int warp,
-                                             T (*red)[BCfg<T, G, NG, RT>::NV][BCfg<T, G, NG, RT>::NW],
-                                             int &buf) {
+                                             int warp, T *red, int &buf) {
     using C = BCfg<T, G, NG, RT>;
     constexpr int E = C::E;
     T p[C::NV];
@@ -140,9 +137,7 @@ __device__ __forceinline__ void backward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
                                               T (&g)[RT][BCfg<T, G, NG, RT>::E],
                                               const T (&v)[BCfg<T, G, NG, RT>::E], T tk,
                                               T *__restrict__ pk, double *sk, int t, int lane,
-                                              int warp,
-                                              T (*red)[BCfg<T, G, NG, RT>::NV][BCfg<T, G, NG, RT>::NW],
-                                              int &buf) {
+                                              int warp, T *red, int &buf) {
     using C = BCfg<T, G, NG, RT>;
     constexpr int E = C::E, VEC = C::VEC;
     T p[C::NV];
@@ -244,7 +239,7 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
     using C = BCfg<T, G, NG, RT>;
     constexpr int E = C::E, VEC = C::VEC, COVER = C::COVER;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[2][C::NV][C::NW];
+    __shared__ T red[2 * C::NV * C::NW];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     T *accp = SMEM ? reinterpret_cast<T *>(smem_raw) : part + (size_t)blockIdx.x * (h + 1) * COVER;
     double *sacc = spart + (size_t)blockIdx.x * h;

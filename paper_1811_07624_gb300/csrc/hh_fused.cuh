@@ -100,6 +100,15 @@ __device__ __forceinline__ T warp_reduce_rows(T (&p)[RT], int lane) {
     return v;
 }
 
+// Flat index of a cross-warp partial in a reduction buffer laid out as
+// [2 buffers][RG groups][NV values][NW warps].  The buffers are plain 1-D shared
+// arrays indexed by this function: a 4-D __shared__ array indexed the same way
+// gave wrong partial sums in one kernel of this library.
+template <int RG, int NV, int NW>
+__device__ __forceinline__ int red_index(int buf, int rg, int v, int w) {
+    return ((buf * RG + rg) * NV + v) * NW + w;
+}
+
 template <typename T, int G, int NG, int RT, int RG>
 struct Cfg {
     static constexpr int VEC = Granule<T>::N;
@@ -116,8 +125,7 @@ struct Cfg {
 template <typename T, int G, int NG, int RT, int RG>
 __device__ __forceinline__ void reflect(T (&x)[RT][Cfg<T, G, NG, RT, RG>::E],
                                         const T *__restrict__ uk, T tk, int t, int lane, int warp,
-                                        int rg,
-                                        T (*red)[RG][RT][Cfg<T, G, NG, RT, RG>::NW], int &buf) {
+                                        int rg, T *red, int &buf) {
     using C = Cfg<T, G, NG, RT, RG>;
     constexpr int VEC = C::VEC, E = C::E, NW = C::NW;
     T u[E];
@@ -146,10 +154,10 @@ __device__ __forceinline__ void reflect(T (&x)[RT][Cfg<T, G, NG, RT, RG>::E],
 #pragma unroll
         for (int r = 0; r < RT; ++r) c[r] = tk * __shfl_sync(0xffffffffu, v, r << SH);
     } else {
-        if ((lane & ((1 << SH) - 1)) == 0) red[buf][rg][lane >> SH][warp] = v;
+        if ((lane & ((1 << SH) - 1)) == 0) red[red_index<RG, RT, NW>(buf, rg, lane >> SH, warp)] = v;
         __syncthreads();
         // lane l < RT*NW reads partial (row l / NW, warp l % NW); segments of NW lanes sum.
-        T q = lane < RT * NW ? red[buf][rg][lane / NW][lane % NW] : T(0);
+        T q = lane < RT * NW ? red[red_index<RG, RT, NW>(buf, rg, lane / NW, lane % NW)] : T(0);
 #pragma unroll
         for (int off = NW / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
 #pragma unroll
@@ -188,7 +196,7 @@ fused_chain_kernel(const T *X, int64_t ldx, T *Y, int64_t ldy, int64_t batch, in
                    const T *__restrict__ sign, const T *__restrict__ d, int vec_ok) {
     using C = Cfg<T, G, NG, RT, RG>;
     constexpr int VEC = C::VEC, E = C::E, NW = C::NW;
-    __shared__ T red[2][RG][RT][NW];
+    __shared__ T red[2 * RG * RT * NW];
     const int tid = threadIdx.x;
     const int rg = tid / G;
     const int t = tid - rg * G;

@@ -11,6 +11,14 @@
 // HH_ERR_INVALID_ARG and that pair's output to NaN.
 #include "hh_fused.cuh"
 
+// (G, NG, RT, RG) of the F32 n <= 4096 configuration.
+#ifndef HH_M4096_G
+#define HH_M4096_G 256
+#define HH_M4096_NG 4
+#define HH_M4096_RT 4
+#define HH_M4096_RG 2
+#endif
+
 namespace hh {
 namespace {
 
@@ -23,7 +31,7 @@ mahalanobis_kernel(const T *X, int64_t ldx, int64_t nrows, const int64_t *__rest
                    int *__restrict__ err) {
     using C = fused::Cfg<T, G, NG, RT, RG>;
     constexpr int VEC = C::VEC, E = C::E, NW = C::NW;
-    __shared__ T red[2][RG][RT][NW];
+    __shared__ T red[2 * RG * RT * NW];
     const int tid = threadIdx.x;
     const int rg = tid / G;
     const int t = tid - rg * G;
@@ -96,9 +104,11 @@ mahalanobis_kernel(const T *X, int64_t ldx, int64_t nrows, const int64_t *__rest
 #pragma unroll
         for (int r = 0; r < RT; ++r) tot[r] = __shfl_sync(0xffffffffu, v, r << SH);
     } else {
-        if ((lane & ((1 << SH) - 1)) == 0) red[buf][rg][lane >> SH][warp] = v;
+        if ((lane & ((1 << SH) - 1)) == 0)
+            red[fused::red_index<RG, RT, NW>(buf, rg, lane >> SH, warp)] = v;
         __syncthreads();
-        T q = lane < RT * NW ? red[buf][rg][lane / NW][lane % NW] : T(0);
+        T q = lane < RT * NW ? red[fused::red_index<RG, RT, NW>(buf, rg, lane / NW, lane % NW)]
+                             : T(0);
 #pragma unroll
         for (int off = NW / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
 #pragma unroll
@@ -141,7 +151,7 @@ hh_status dispatch(const Plan *p, const void *X, int64_t ldx, int64_t nrows, con
         else if (n <= 512) HH_M(32, 4, 4, 8);
         else if (n <= 1024) HH_M(64, 4, 4, 4);
         else if (n <= 2048) HH_M(128, 4, 4, 2);
-        else if (n <= 4096) HH_M(256, 4, 4, 2);
+        else if (n <= 4096) HH_M(HH_M4096_G, HH_M4096_NG, HH_M4096_RT, HH_M4096_RG);
         else return fail(HH_ERR_UNSUPPORTED, "mahalanobis: n = %lld above 4096 (F32)", (long long)n);
     } else {
         if (n <= 64) HH_M(32, 1, 2, 8);

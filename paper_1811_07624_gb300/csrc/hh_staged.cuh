@@ -124,8 +124,7 @@ template <int G, int NG, int RT, int RG, int B>
 __device__ __forceinline__ void chain(
     float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E2], bool asc, int h, const float *__restrict__ V,
     int64_t ldv, const float *__restrict__ tau, const float *__restrict__ gram, int t, int lane,
-    int warp, int rg,
-    float (*red)[RG][SCfg<G, NG, RT, RG, B>::NV][SCfg<G, NG, RT, RG, B>::NW], int &buf) {
+    int warp, int rg, float *red, int &buf) {
     using C = SCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L;
     for (int s = 0; s < h; s += B) {
@@ -178,12 +177,12 @@ __device__ __forceinline__ void chain(
 #pragma unroll
             for (int q = 0; q < NV; ++q) z[q] = __shfl_sync(0xffffffffu, v, q * L);
         } else {
-            if ((lane & (L - 1)) == 0) red[buf][rg][lane / L][warp] = v;
+            if ((lane & (L - 1)) == 0) red[fused::red_index<RG, NV, NW>(buf, rg, lane / L, warp)] = v;
             __syncthreads();
             const int idx = lane / L, sub = lane & (L - 1);
             float q = 0.f;
 #pragma unroll
-            for (int w = sub; w < NW; w += L) q += red[buf][rg][idx][w];
+            for (int w = sub; w < NW; w += L) q += red[fused::red_index<RG, NV, NW>(buf, rg, idx, w)];
 #pragma unroll
             for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
 #pragma unroll
@@ -239,7 +238,7 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
     constexpr int E2 = C::E2, ROWS = C::ROWS;
     extern __shared__ __align__(128) float stage[];  // ROWS x n
     __shared__ __align__(8) uint64_t full_bar;
-    __shared__ float red[2][RG][C::NV][C::NW];
+    __shared__ float red[2 * RG * C::NV * C::NW];
     __shared__ int aborted;
 
     const int tid = threadIdx.x;
