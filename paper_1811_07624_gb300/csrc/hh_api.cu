@@ -44,6 +44,7 @@ static bool device_ptr(const void *p, int dev) {
 
 static void free_plan(Plan *p) {
     if (!p) return;
+    wy_free(p);
     cudaFree(p->u);
     cudaFree(p->d);
     cudaFree(p->sign);
@@ -90,6 +91,7 @@ static hh_status apply_common(hh_plan_t plan, hh_mode mode, const void *X, int64
     if (batch == 0) return HH_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (p->path == HH_PATH_FUSED) return fused_apply(p, mode, X, ldx, Y, ldy, batch, s);
+    if (p->path == HH_PATH_WY) return wy_apply(p, mode, X, ldx, Y, ldy, batch, s);
     return fail(HH_ERR_UNSUPPORTED, "no kernel for this plan's path");
 }
 
@@ -151,8 +153,8 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
     if (path == HH_PATH_AUTO) path = dtype == HH_BF16 ? HH_PATH_WY : HH_PATH_FUSED;
     if (path == HH_PATH_FUSED && dtype == HH_BF16)
         return fail(HH_ERR_UNSUPPORTED, "the fused path computes in F32 or F64");
-    if (path == HH_PATH_WY)
-        return fail(HH_ERR_UNSUPPORTED, "the compact-WY path is not built in this version");
+    if (path == HH_PATH_WY && dtype != HH_BF16)
+        return fail(HH_ERR_UNSUPPORTED, "the compact-WY path computes in BF16");
     if (h > 0 && ldu < n)
         return fail(HH_ERR_INVALID_ARG, "ldu = %lld < n = %lld", (long long)ldu, (long long)n);
     int dev = 0;
@@ -197,7 +199,12 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
         st = cuda_fail(e, "cudaMemsetAsync");
         goto done;
     }
-    st = prepare_fused(p, U, ldu, d, sign, flag, s);
+    if (path == HH_PATH_WY) {
+        st = wy_prepare(p, U, ldu, sign, flag, s);
+        if (!st) st = wy_prepare_sign(p, sign, flag, s);
+    } else {
+        st = prepare_fused(p, U, ldu, d, sign, flag, s);
+    }
     if (st) goto done;
     {
         int hflag = 0;
@@ -206,6 +213,7 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
             st = cuda_fail(e, "plan preparation");
             goto done;
         }
+        if (path == HH_PATH_WY) wy_release_workspace(p);
         if (hflag & 1) st = fail(HH_ERR_NONFINITE, "U holds a NaN or Inf");
         else if (hflag & 2) st = fail(HH_ERR_NONFINITE, "d holds a NaN or Inf");
         else if (hflag & 4) st = fail(HH_ERR_INVALID_ARG, "sign holds a value other than +1/-1");

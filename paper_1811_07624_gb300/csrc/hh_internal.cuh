@@ -60,6 +60,15 @@ inline size_t dtype_size(hh_dtype t) {
 hh_status prepare_fused(Plan *p, const void *U, int64_t ldu, const void *d, const int8_t *sign,
                         int *bad_flag, cudaStream_t st);
 
+// ---- compact-WY path on the tensor cores (hh_wy.cu), BF16 plans ----
+hh_status wy_prepare(Plan *p, const void *U, int64_t ldu, const int8_t *sign, int *flag,
+                     cudaStream_t st);
+hh_status wy_prepare_sign(Plan *p, const int8_t *sign, int *flag, cudaStream_t st);
+void wy_release_workspace(Plan *p);
+void wy_free(Plan *p);
+hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                   int64_t batch, cudaStream_t st);
+
 // ---- fused apply (hh_fused.cu) ----
 hh_status fused_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void *Y,
                       int64_t ldy, int64_t batch, cudaStream_t st);
