@@ -5,9 +5,9 @@
 //     H_1 ... H_m = I - V T V^T,   V = [v_1 .. v_m],
 // with T upper triangular, T_kk = tau_k, T[0:k, k] = -tau_k T[0:k, 0:k] V[:, 0:k]^T v_k
 // (the forward accumulation of Schreiber and Van Loan).  For vectors stored as
-// rows, Y = X W^T = X - (X V) (V T^T)^T, i.e. two GEMMs:
+// rows, Y = X W^T = X - (X V) T^T V^T = X - (X V) (V T)^T, i.e. two GEMMs:
 //     Z = X V          (M = rows, N = m, K = n)
-//     Y = X - Z V'^T   (M = rows, N = n, K = m),  V' = V T^T   (W^T: V' = V T).
+//     Y = X - Z V'^T   (M = rows, N = n, K = m),  V' = V T   (W^T: V' = V T^T).
 // The paper's 4nm operations per vector (§II-A) are exactly these two GEMMs.
 //
 // The chain is cut into panels of at most 256 reflectors (a panel's Z fits in
@@ -39,8 +39,8 @@ struct WYPlan {
     int64_t n8 = 0;          // row stride of the BF16 reflector copies (n rounded up to 8)
     __nv_bfloat16 *Vb = nullptr;    // hpad x n8, v_k as given (zero rows past h)
     __nv_bfloat16 *Vs = nullptr;    // sign-scaled copy (W^T, first panel), or null
-    __nv_bfloat16 *Vp = nullptr;    // P x n x PB: V_p T_p^T (W)
-    __nv_bfloat16 *Vpp = nullptr;   // P x n x PB: V_p T_p   (W^T)
+    __nv_bfloat16 *Vp = nullptr;    // P x n x PB: V_p T_p^T (operand of W^T)
+    __nv_bfloat16 *Vpp = nullptr;   // P x n x PB: V_p T_p   (operand of W)
     float *sign = nullptr;          // n, or null
     double *V64 = nullptr, *G = nullptr, *T = nullptr;  // create-time work arrays
     CUtensorMap mapV, mapVs, mapVp, mapVpp;  // tensor maps of Vb, Vs, Vp, Vpp
@@ -509,7 +509,8 @@ hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void
         a.sign_in = mode == HH_MODE_WT && i == 0 && w->sign;
         a.err = p->err;
         const CUtensorMap &mv = a.sign_in ? w->mapVs : w->mapV;
-        const CUtensorMap &mvp = mode == HH_MODE_W ? w->mapVp : w->mapVpp;
+        // W: Y = X - Z (V T)^T; W^T: Y = X - Z (V T^T)^T
+        const CUtensorMap &mvp = mode == HH_MODE_W ? w->mapVpp : w->mapVp;
         wy::wy_panel_kernel<<<(unsigned)tiles, wy::kThreads, wy::kSmemBytes, st>>>(mapX, mv, mvp, a);
         cudaError_t e = cudaGetLastError();
         if (e) return cuda_fail(e, "compact-WY launch");
