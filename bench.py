@@ -1,24 +1,31 @@
-"""Throughput of the Householder-chain transforms on GB300.
+"""Throughput of the Householder-chain hot path on GB300.
 
-One step = one pass of every built hot-path row over one resident batch of
-synthetic vectors: for the FP32 chain at n=4096, h=16, batch 262,144 the
-kernels y = W x, y = W^T x and y = S x (S = D W diag(d) W^T D), each reading
-and writing every vector once.  `value` is vectors per second through the
-whole step (all ranks), timed with CUDA events on the launching stream.
+One step = one pass of every built hot-path row over its own resident batch of
+synthetic vectors (inputs larger than L2, so no flush is needed):
 
-    python bench.py [--steps K] [--warmup W] [--impl ours|reference]
-                    [--gpus N] [--no-e2e] [--no-cpu]
+  chain_W, chain_WT, chain_SYM   FP32 chain, n=4096, h=16, 262,144 vectors:
+                                 y = sigma.*(W x), W^T(sigma.*x), sigma.*W(d.*W^T(sigma.*x))
+  wy_h64, wy_h256, wy_h1024      BF16 compact-WY (tcgen05), n=4096, 262,144 vectors, y = W x
+  mahalanobis                    FP32 fast Mahalanobis distance, n=256, h=16, 1,048,576 pairs
+  mahalanobis_grad               its gradient w.r.t. U and d (metric-learning loss)
+  adjoint_SYM                    FP32 forward + adjoint of S x, n=1024, h=32, 65,536 vectors
 
-With torchrun (N > 1) each rank runs its own replica of the workload (the
-transforms share nothing across vectors, so there is no collective on the
-data path); rank 0 prints the JSON line.  `--impl reference` times the FP64
-CPU oracle on a bounded sample of the same workload.
+`value` is vectors per second through the whole step (the sum of the rows'
+vectors over the step time), timed with CUDA events on the launching stream.
+Each row also reports its own time, vectors/s, algorithmic GB/s and FLOP/s
+and roofline fraction; the FP32 chain on the WY rows' shapes and data is
+timed beside them ("BF16-WY vs FP32 plain").  `--impl reference` times the
+FP64 CPU oracle on a bounded sample of the same rows.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--gpus N]
+                    [--rows a,b,...] [--batch-scale f] [--no-e2e] [--no-cpu] [--no-compare]
 """
 
 from __future__ import annotations
 
 import argparse
 import csv
+import hashlib
 import io
 import json
 import os
@@ -33,37 +40,36 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "vectors/s + HBM GB/s % of peak, Householder-chain apply, BF16-WY vs FP32 plain"
-WORKLOAD = dict(n=4096, h=16, batch=262_144, seed=0)
-ROWS = ("W", "WT", "SYM")
+N_CHAIN, H_CHAIN, B_CHAIN = 4096, 16, 262_144
+B_WY = 262_144
+N_MAHAL, H_MAHAL, P_MAHAL, PTS_MAHAL = 256, 16, 1 << 20, 100_000
+N_ADJ, H_ADJ, B_ADJ = 1024, 32, 65_536
+ALL_ROWS = ["chain_W", "chain_WT", "chain_SYM", "wy_h64", "wy_h256", "wy_h1024", "mahalanobis",
+            "mahalanobis_grad", "adjoint_SYM"]
+
+KERNEL_SOURCES = ["paper_1811_07624_gb300/csrc/hh_staged.cuh",
+                  "paper_1811_07624_gb300/csrc/hh_fused_f32.cu",
+                  "paper_1811_07624_gb300/csrc/hh_fused.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "staged_chain_n4096_h16_ncu_full.md")
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            j = json.load(f)
-        return j, "of measured"
+            return json.load(f), "of measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
             "sm_max_mhz": 2070.0}, "of fallback"
 
 
-KERNEL_SOURCES = ["paper_1811_07624_gb300/csrc/hh_staged.cuh", "paper_1811_07624_gb300/csrc/hh_fused_f32.cu",
-                  "paper_1811_07624_gb300/csrc/hh_fused.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "staged_chain_n4096_h16_ncu_full.md")
-
-
 def profiled_traffic(mode, batch):
-    """DRAM bytes of one launch from the committed ncu summary, scaled by the
-    vector count; None when the kernel sources changed since the capture."""
-    import hashlib
-
+    """DRAM bytes of one chain launch from the committed ncu summary, scaled by
+    the vector count; None when the kernel sources changed since the capture."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
@@ -79,17 +85,6 @@ def profiled_traffic(mode, batch):
     return None
 
 
-def algorithmic(mode, n, h, batch, esize=4):
-    """Bytes and flops one launch must move / do (the paper's op counts)."""
-    bytes_ = 2 * batch * n * esize + h * n * esize
-    if mode == "SYM":
-        bytes_ += n * esize
-        flops = (8 * h + 1) * n * batch  # §III-A
-    else:
-        flops = 4 * n * h * batch  # §II-A
-    return bytes_, flops
-
-
 class ClockSampler:
     """nvidia-smi SM-clock samples while the timed region runs."""
 
@@ -98,8 +93,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
+        self.gpu, self.proc = gpu_index, None
 
     def start(self):
         try:
@@ -120,7 +114,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for row in csv.reader(io.StringIO(out)):
             if len(row) < 9:
@@ -128,6 +122,7 @@ class ClockSampler:
             try:
                 sm.append(float(row[1]))
                 mx.append(float(row[2]))
+                pw.append(float(row[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, row[5:9]):
@@ -135,113 +130,439 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "power_w_max": max(pw) if pw else None, "samples": len(sm)}
 
 
-def oracle_sample_rate(workload, rows, budget_s=12.0, threads=0):
-    """Vectors/s of the FP64 oracle through `rows` on a bounded sample."""
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+# --------------------------------------------------------------------------------------
+# rows: resident inputs, one call per step
+
+_SHARED = {}
+
+
+class ChainRow:
+    def __init__(self, torch, dev, mode, n, h, batch, seed=0):
+        import synthetic_inputs as si
+        from paper_1811_07624_gb300 import Plan
+
+        self.name, self.mode, self.n, self.h, self.B = f"chain_{mode}", mode, n, h, batch
+        self.U = si.reflectors(n, h, seed=seed)
+        self.d = si.spectrum(n, seed=seed)
+        self.s = si.sign(n, seed=seed)
+        self.plan = Plan(torch.tensor(self.U, device=dev, dtype=torch.float32),
+                         d=torch.tensor(self.d, device=dev, dtype=torch.float32),
+                         sign=torch.tensor(self.s, device=dev))
+        key = (n, batch, seed)
+        if key not in _SHARED:  # the three chain rows read the same vectors
+            g = torch.Generator(device=dev).manual_seed(seed + 1)
+            _SHARED[key] = torch.randn(batch, n, device=dev, generator=g)
+        self.X = _SHARED[key]
+        self.Y = torch.empty_like(self.X)
+        self.torch = torch
+        self.launches = 1
+        self.bound = "hbm" if (self.flops() / self.bytes()) < 11.9 else "alu"
+
+    def vectors(self):
+        return self.B
+
+    def bytes(self):
+        return 2.0 * self.B * self.n * 4 + self.h * self.n * 4
+
+    def flops(self):
+        per = (8 * self.h + 1) * self.n if self.mode == "SYM" else 4 * self.n * self.h
+        return float(per) * self.B
+
+    def run(self):
+        self.plan.apply_mode(self.mode, self.X, out=self.Y)
+
+    def parity(self):
+        import oracle
+
+        t = self.torch
+        idx = t.linspace(0, self.B - 1, 64, device=self.X.device).long()
+        ref = oracle.apply(self.mode, t.tensor(self.U, dtype=t.float32).double().numpy(),
+                           self.X[idx].double().cpu().numpy(), sign=self.s,
+                           d=t.tensor(self.d, dtype=t.float32).double().numpy())
+        return rel_l2(self.Y[idx].double().cpu().numpy(), ref)
+
+    def e2e(self, torch):
+        key = ("host", self.n, self.B)
+        if key not in _SHARED:
+            Xh = self.X.cpu().pin_memory()
+            _SHARED[key] = (Xh, torch.empty_like(Xh).pin_memory(), torch.empty_like(self.X),
+                            torch.empty_like(self.X))
+        Xh, Yh, Xd, Yd = _SHARED[key]
+
+        def step():
+            Xd.copy_(Xh, non_blocking=True)
+            self.plan.apply_mode(self.mode, Xd, out=Yd)
+            Yh.copy_(Yd, non_blocking=True)
+        return Xh.numel() * 4, Yh.numel() * 4, step
+
+
+class WYRow:
+    def __init__(self, torch, dev, n, h, batch, seed=0):
+        import synthetic_inputs as si
+        from paper_1811_07624_gb300 import Plan
+
+        self.name, self.n, self.h, self.B = f"wy_h{h}", n, h, batch
+        self.U = si.reflectors(n, h, seed=seed + h)
+        self.Ub = torch.tensor(self.U, device=dev, dtype=torch.bfloat16)
+        self.plan = Plan(self.Ub)
+        h64 = -(-h // 64) * 64
+        self.launches = -(-h64 // 256)  # one launch per panel of <= 256 reflectors
+        g = torch.Generator(device=dev).manual_seed(seed + h + 1)
+        self.X = torch.randn(batch, n, device=dev, generator=g).bfloat16()
+        self.Y = torch.empty_like(self.X)
+        self.torch = torch
+        ridge = 1700.6e12 / 6765.7e9
+        self.bound = "hbm" if self.flops() / self.bytes() < ridge else "tensor"
+
+    def vectors(self):
+        return self.B
+
+    def bytes(self):
+        return 2.0 * self.B * self.n * 2 + self.h * self.n * 2
+
+    def flops(self):
+        return 4.0 * self.n * self.h * self.B
+
+    def run(self):
+        self.plan.apply(self.X, out=self.Y)
+
+    def parity(self):
+        import oracle
+
+        t = self.torch
+        idx = t.linspace(0, self.B - 1, 32, device=self.X.device).long()
+        ref = oracle.apply("W", self.Ub.double().cpu().numpy(), self.X[idx].double().cpu().numpy())
+        return rel_l2(self.Y[idx].double().cpu().numpy(), ref)
+
+    def e2e(self, torch):
+        Xh = self.X.cpu().pin_memory()
+        Yh = torch.empty_like(Xh).pin_memory()
+        Xd, Yd = torch.empty_like(self.X), torch.empty_like(self.X)
+
+        def step():
+            Xd.copy_(Xh, non_blocking=True)
+            self.plan.apply(Xd, out=Yd)
+            Yh.copy_(Yd, non_blocking=True)
+        return Xh.numel() * 2, Yh.numel() * 2, step
+
+
+class MahalanobisRow:
+    def __init__(self, torch, dev, grad=False, seed=0):
+        import synthetic_inputs as si
+        from paper_1811_07624_gb300 import Plan
+
+        self.name = "mahalanobis_grad" if grad else "mahalanobis"
+        self.grad = grad
+        self.n, self.h, self.P = N_MAHAL, H_MAHAL, P_MAHAL
+        X, labels = si.gaussian_mixture(PTS_MAHAL, n=self.n, seed=seed)
+        ia, ib, _ = si.labelled_pairs(labels, self.P, seed=seed)
+        self.U = si.reflectors(self.n, self.h, seed=seed + 7)
+        self.d = si.spectrum(self.n, seed=seed + 7)
+        self.ia_np, self.ib_np = ia, ib
+        self.X = torch.tensor(X, device=dev, dtype=torch.float32)
+        self.ia = torch.tensor(ia, device=dev)
+        self.ib = torch.tensor(ib, device=dev)
+        self.plan = Plan(torch.tensor(self.U, device=dev, dtype=torch.float32),
+                         d=torch.tensor(self.d, device=dev, dtype=torch.float32))
+        self.out = torch.empty(self.P, device=dev)
+        self.gout = torch.ones(self.P, device=dev) / self.P
+        self.torch = torch
+        self.launches = 2 if grad else 1
+        self.bound = "alu" if grad else "hbm"
+
+    def vectors(self):
+        return self.P
+
+    def bytes(self):
+        return 2.0 * self.P * self.n * 4 + self.P * (16 + 4)
+
+    def flops(self):
+        per = 4 * self.n * self.h + 3 * self.n
+        return float(per) * self.P * (4 if self.grad else 1)
+
+    def run(self):
+        if self.grad:
+            self.plan.mahalanobis_backward(self.X, self.ia, self.ib, self.gout)
+        else:
+            self.plan.mahalanobis(self.X, self.ia, self.ib, out=self.out)
+
+    def parity(self):
+        import oracle
+
+        t = self.torch
+        sel = np.linspace(0, self.P - 1, 256).astype(np.int64)
+        selt = t.tensor(sel, device=self.X.device)
+        U32 = t.tensor(self.U, dtype=t.float32).double().numpy()
+        d32 = t.tensor(self.d, dtype=t.float32).double().numpy()
+        X32 = self.X.double().cpu().numpy()
+        if not self.grad:
+            self.plan.mahalanobis(self.X, self.ia, self.ib, out=self.out)
+            ref = oracle.mahalanobis(U32, X32, self.ia_np[sel], self.ib_np[sel], d32)
+            return rel_l2(self.out[selt].double().cpu().numpy(), ref)
+        gU, gd = self.plan.mahalanobis_backward(self.X, self.ia[selt], self.ib[selt],
+                                                t.ones(sel.shape[0], device=self.X.device))
+        delta = X32[self.ia_np[sel]] - X32[self.ib_np[sel]]
+        z = oracle.apply("WT", U32, delta)
+        _, gU_ref, _ = oracle.backward("WT", U32, delta, 2.0 * d32[None, :] * z)
+        return max(rel_l2(gU.double().cpu().numpy(), gU_ref),
+                   rel_l2(gd.double().cpu().numpy(), (z * z).sum(0)))
+
+    def e2e(self, torch):
+        Xh = self.X.cpu().pin_memory()
+        iah, ibh = self.ia.cpu().pin_memory(), self.ib.cpu().pin_memory()
+        oh = torch.empty(self.P).pin_memory()
+        gUh = torch.empty(self.h, self.n).pin_memory()
+        Xd, iad, ibd = torch.empty_like(self.X), torch.empty_like(self.ia), torch.empty_like(self.ib)
+
+        def step():
+            Xd.copy_(Xh, non_blocking=True)
+            iad.copy_(iah, non_blocking=True)
+            ibd.copy_(ibh, non_blocking=True)
+            if self.grad:
+                gU, _ = self.plan.mahalanobis_backward(Xd, iad, ibd, self.gout)
+                gUh.copy_(gU, non_blocking=True)
+            else:
+                self.plan.mahalanobis(Xd, iad, ibd, out=self.out)
+                oh.copy_(self.out, non_blocking=True)
+        h2d = Xh.numel() * 4 + 2 * iah.numel() * 8
+        d2h = gUh.numel() * 4 if self.grad else oh.numel() * 4
+        return h2d, d2h, step
+
+
+class AdjointRow:
+    def __init__(self, torch, dev, seed=0):
+        import synthetic_inputs as si
+        from paper_1811_07624_gb300 import Plan
+
+        self.name = "adjoint_SYM"
+        self.n, self.h, self.B = N_ADJ, H_ADJ, B_ADJ
+        self.U = si.reflectors(self.n, self.h, seed=seed + 9)
+        self.d = si.spectrum(self.n, seed=seed + 9)
+        self.plan = Plan(torch.tensor(self.U, device=dev, dtype=torch.float32),
+                         d=torch.tensor(self.d, device=dev, dtype=torch.float32))
+        g = torch.Generator(device=dev).manual_seed(seed + 10)
+        self.X = torch.randn(self.B, self.n, device=dev, generator=g)
+        self.G = torch.randn(self.B, self.n, device=dev, generator=g)
+        self.Y = torch.empty_like(self.X)
+        self.torch = torch
+        self.launches = 3  # forward, adjoint, fixed-order reduction
+        self.bound = "alu"
+
+    def vectors(self):
+        return self.B
+
+    def bytes(self):
+        return 4.0 * self.B * self.n * 4
+
+    def flops(self):
+        # forward S x, (8h+1) n, and the adjoint: its recomputed forward plus about
+        # three times the forward arithmetic
+        return float((8 * self.h + 1) * self.n * 5) * self.B
+
+    def run(self):
+        self.plan.apply_sym(self.X, out=self.Y)
+        self.res = self.plan.backward("SYM", self.X, self.G)
+
+    def parity(self):
+        import oracle
+
+        t = self.torch
+        sub = 64
+        gX, gU, gd = self.plan.backward("SYM", self.X[:sub].contiguous(), self.G[:sub].contiguous())
+        U32 = t.tensor(self.U, dtype=t.float32).double().numpy()
+        d32 = t.tensor(self.d, dtype=t.float32).double().numpy()
+        rX, rU, rd = oracle.backward("SYM", U32, self.X[:sub].double().cpu().numpy(),
+                                     self.G[:sub].double().cpu().numpy(), d=d32)
+        return max(rel_l2(gX.double().cpu().numpy(), rX), rel_l2(gU.double().cpu().numpy(), rU),
+                   rel_l2(gd.double().cpu().numpy(), rd))
+
+    def e2e(self, torch):
+        Xh, Gh = self.X.cpu().pin_memory(), self.G.cpu().pin_memory()
+        gUh = torch.empty(self.h, self.n).pin_memory()
+        Xd, Gd = torch.empty_like(self.X), torch.empty_like(self.G)
+
+        def step():
+            Xd.copy_(Xh, non_blocking=True)
+            Gd.copy_(Gh, non_blocking=True)
+            self.plan.apply_sym(Xd, out=self.Y)
+            _, gU, _ = self.plan.backward("SYM", Xd, Gd, need_gX=False)
+            gUh.copy_(gU, non_blocking=True)
+        return (Xh.numel() + Gh.numel()) * 4, gUh.numel() * 4, step
+
+
+def make_rows(torch, dev, names):
+    rows = []
+    for nm in names:
+        if nm.startswith("chain_"):
+            rows.append(ChainRow(torch, dev, nm.split("_")[1], N_CHAIN, H_CHAIN, B_CHAIN))
+        elif nm.startswith("wy_h"):
+            rows.append(WYRow(torch, dev, N_CHAIN, int(nm[4:]), B_WY))
+        elif nm == "mahalanobis":
+            rows.append(MahalanobisRow(torch, dev, grad=False))
+        elif nm == "mahalanobis_grad":
+            rows.append(MahalanobisRow(torch, dev, grad=True))
+        elif nm == "adjoint_SYM":
+            rows.append(AdjointRow(torch, dev))
+        else:
+            raise ValueError(f"unknown row {nm}")
+    return rows
+
+
+def scale_batches(f):
+    global B_CHAIN, B_WY, P_MAHAL, B_ADJ
+    B_CHAIN, B_WY = max(1, int(B_CHAIN * f)), max(1, int(B_WY * f))
+    P_MAHAL, B_ADJ = max(1, int(P_MAHAL * f)), max(1, int(B_ADJ * f))
+
+
+def config_dict(names):
+    return {"workload": "Householder-chain hot path, one step = every row once: FP32 chain "
+                        f"n={N_CHAIN} h={H_CHAIN} batch={B_CHAIN} (W, W^T, S); BF16 compact-WY "
+                        f"n={N_CHAIN} h=64/256/1024 batch={B_WY} (W); fast Mahalanobis n={N_MAHAL} "
+                        f"h={H_MAHAL} {P_MAHAL} pairs (+ gradient); adjoint of S n={N_ADJ} "
+                        f"h={H_ADJ} batch={B_ADJ}",
+            "rows": list(names), "l2": "every row's inputs are larger than L2 (no flush)",
+            "parallelism": "replicas (one independent copy per rank)"}
+
+
+# --------------------------------------------------------------------------------------
+# FP64 oracle on the host cores (cpu_baseline, --impl reference)
+
+
+def oracle_units(names):
+    """Host-only workloads of the rows (same shapes and seeds), each a function of
+    a unit count returning nothing; units are vectors (or pairs)."""
     import oracle
     import synthetic_inputs as si
 
-    n, h = workload["n"], workload["h"]
-    U = si.reflectors(n, h, seed=workload["seed"])
-    d = si.spectrum(n, seed=workload["seed"])
-    s = si.sign(n, seed=workload["seed"])
+    fns = {}
+    for nm in names:
+        if nm.startswith("chain_"):
+            mode = nm.split("_")[1]
+            U, d, s = (si.reflectors(N_CHAIN, H_CHAIN), si.spectrum(N_CHAIN),
+                       si.sign(N_CHAIN))
+            Xs = si.vectors(1024, N_CHAIN, seed=123)
+            fns[nm] = lambda c, m=mode, U=U, d=d, s=s, Xs=Xs: oracle.apply(
+                m, U, np.resize(Xs, (c, N_CHAIN)), sign=s, d=d)
+        elif nm.startswith("wy_h"):
+            h = int(nm[4:])
+            U = si.reflectors(N_CHAIN, h, seed=h)
+            Xs = si.vectors(64, N_CHAIN, seed=124)
+            fns[nm] = lambda c, U=U, Xs=Xs: oracle.apply("W", U, np.resize(Xs, (c, N_CHAIN)))
+        elif nm.startswith("mahalanobis"):
+            X, labels = si.gaussian_mixture(20_000, n=N_MAHAL, seed=0)
+            ia, ib, _ = si.labelled_pairs(labels, 1 << 16, seed=0)
+            U, d = si.reflectors(N_MAHAL, H_MAHAL, seed=7), si.spectrum(N_MAHAL, seed=7)
+            if nm.endswith("grad"):
+                def f(c, X=X, ia=ia, ib=ib, U=U, d=d):
+                    sel = np.arange(c) % ia.shape[0]
+                    delta = X[ia[sel]] - X[ib[sel]]
+                    z = oracle.apply("WT", U, delta)
+                    oracle.backward("WT", U, delta, 2.0 * d[None, :] * z)
+            else:
+                def f(c, X=X, ia=ia, ib=ib, U=U, d=d):
+                    sel = np.arange(c) % ia.shape[0]
+                    oracle.mahalanobis(U, X, ia[sel], ib[sel], d)
+            fns[nm] = f
+        elif nm == "adjoint_SYM":
+            U, d = si.reflectors(N_ADJ, H_ADJ, seed=9), si.spectrum(N_ADJ, seed=9)
+            Xs, Gs = si.vectors(256, N_ADJ, seed=125), si.vectors(256, N_ADJ, seed=126)
 
-    def run(count):
-        X = si.vectors(count, n, seed=123)
+            def f(c, U=U, d=d, Xs=Xs, Gs=Gs):
+                X, G = np.resize(Xs, (c, N_ADJ)), np.resize(Gs, (c, N_ADJ))
+                oracle.apply("SYM", U, X, d=d)
+                oracle.backward("SYM", U, X, G, d=d)
+            fns[nm] = f
+    return fns
+
+
+def oracle_rates(names, budget_s):
+    """Per row: (units, seconds) of the oracle on a bounded sample."""
+    fns = oracle_units(names)
+    out = {}
+    for nm, f in fns.items():
         t0 = time.perf_counter()
-        for mode in rows:
-            oracle.apply(mode, U, X, sign=s, d=d, threads=threads)
-        return time.perf_counter() - t0
-
-    probe = 256
-    t = run(probe)
-    count = int(max(probe, min(1 << 20, probe * budget_s / max(t, 1e-6))))
-    t = run(count)
-    return count / t, count, t
+        f(4)
+        dt = max(time.perf_counter() - t0, 1e-4)
+        count = int(max(4, min(1 << 18, 4 * budget_s / dt)))
+        t0 = time.perf_counter()
+        f(count)
+        out[nm] = (count, time.perf_counter() - t0)
+    return out, fns
 
 
-def run_reference(args):
-    rank, world, _ = dist_env()
+def step_vectors(names):
+    per = {"chain": B_CHAIN, "wy": B_WY, "mahalanobis": P_MAHAL, "adjoint": B_ADJ}
+    return {nm: per[nm.split("_")[0]] for nm in names}
+
+
+def run_reference(args, names):
+    """The FP64 oracle on the host cores: each step runs a bounded sample of every
+    row (about half a second of work each); the full step's time is the sum of
+    the rows' per-unit times times their full batches."""
+    rank, _, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
 
     threads = oracle.max_threads()
-    _, count, t = oracle_sample_rate(WORKLOAD, ROWS, budget_s=2.0)
-    per_step = count
-    times = []
+    rates, fns = oracle_rates(names, budget_s=0.3)
+    units = {nm: max(1, int(c / t * 0.5)) for nm, (c, t) in rates.items()}
+    full = step_vectors(names)
+    per_unit = {nm: [] for nm in names}
     for i in range(args.warmup + args.steps):
-        rate, c, dt = oracle_sample_rate_fixed(WORKLOAD, ROWS, per_step)
-        if i >= args.warmup:
-            times.append(dt)
-    ms = 1e3 * sum(times) / len(times)
-    value = per_step / (ms / 1e3)
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(),
-        "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{per_step} vectors per step through W, W^T and S (FP64 oracle)"},
-        "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
+        for nm, f in fns.items():
+            t0 = time.perf_counter()
+            f(units[nm])
+            if i >= args.warmup:
+                per_unit[nm].append((time.perf_counter() - t0) / units[nm])
+    step_s = sum(full[nm] * statistics.mean(per_unit[nm]) for nm in names)
+    value = sum(full.values()) / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian vectors, reflectors and mixture)",
+            "config": config_dict(names),
+            "cpu_baseline": {"value": value, "unit": "vectors/s", "cores": threads, "kind": "oracle",
+                             "sample": "per step, units of each row: "
+                                       + ", ".join(f"{k} {v}" for k, v in units.items())
+                                       + "; the full step's time is extrapolated per unit"},
+            "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-_REF_CACHE = {}
-
-
-def oracle_sample_rate_fixed(workload, rows, count):
-    import oracle
-    import synthetic_inputs as si
-
-    key = (workload["n"], workload["h"], count)
-    if key not in _REF_CACHE:
-        n, h = workload["n"], workload["h"]
-        _REF_CACHE[key] = (si.reflectors(n, h, seed=workload["seed"]),
-                           si.spectrum(n, seed=workload["seed"]),
-                           si.sign(n, seed=workload["seed"]), si.vectors(count, n, seed=123))
-    U, d, s, X = _REF_CACHE[key]
-    t0 = time.perf_counter()
-    for mode in rows:
-        oracle.apply(mode, U, X, sign=s, d=d)
-    dt = time.perf_counter() - t0
-    return count / dt, count, dt
-
-
-def config_dict():
-    w = WORKLOAD
-    return {"workload": f"FP32 fused reflector chain n={w['n']} h={w['h']} batch={w['batch']}: "
-                        "y = W x, y = W^T x, y = W diag(d) W^T x per vector (sign D on)",
-            "n": w["n"], "h": w["h"], "batch": w["batch"], "rows": list(ROWS),
-            "l2": "inputs larger than L2 (4.3 GB per buffer), no flush needed",
-            "parallelism": "replicas"}
+# --------------------------------------------------------------------------------------
 
 
 def main():
-    global ROWS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rows", default=",".join(ALL_ROWS))
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="scale every row's batch (profiling a smaller case; not a bench line)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--batch", type=int, default=None,
-                    help="override the batch (profiling a smaller case); not a bench line")
-    ap.add_argument("--rows", default=",".join(ROWS), help="subset of W,WT,SYM to run")
+    ap.add_argument("--no-compare", action="store_true")
     args = ap.parse_args()
-    ROWS = tuple(r for r in args.rows.split(",") if r)
-    if args.batch:
-        WORKLOAD["batch"] = args.batch
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
+    names = [r for r in args.rows.split(",") if r]
+    if args.batch_scale != 1.0:
+        scale_batches(args.batch_scale)
     if args.impl == "reference":
-        return run_reference(args)
+        return run_reference(args, names)
 
     import torch
 
@@ -257,144 +578,161 @@ def main():
 
     __graft_entry__.build()
     import oracle
-    import synthetic_inputs as si
-    from paper_1811_07624_gb300 import Plan
 
     dev = torch.device("cuda", local)
-    n, h, B, seed = WORKLOAD["n"], WORKLOAD["h"], WORKLOAD["batch"], WORKLOAD["seed"]
-    U = si.reflectors(n, h, seed=seed)
-    d = si.spectrum(n, seed=seed)
-    s = si.sign(n, seed=seed)
-    plan = Plan(torch.tensor(U, device=dev, dtype=torch.float32),
-                d=torch.tensor(d, device=dev, dtype=torch.float32), sign=torch.tensor(s, device=dev))
-    g = torch.Generator(device=dev).manual_seed(seed + 1000 * rank)
-    X = torch.randn(B, n, device=dev, generator=g, dtype=torch.float32)
-    Ys = {m: torch.empty_like(X) for m in ROWS}
-    fns = {"W": plan.apply, "WT": plan.apply_T, "SYM": plan.apply_sym}
+    rows = make_rows(torch, dev, names)
     stream = torch.cuda.current_stream()
 
-    # parity on sampled rows, outside the timed region
-    for m in ROWS:
-        fns[m](X, out=Ys[m])
+    for r in rows:  # first call and parity on sampled outputs, outside the timed region
+        r.run()
     torch.cuda.synchronize()
-    idx = np.linspace(0, B - 1, 64).astype(np.int64)
-    Xs = X[idx].double().cpu().numpy()
-    U32 = torch.tensor(U, dtype=torch.float32).double().numpy()
-    d32 = torch.tensor(d, dtype=torch.float32).double().numpy()
-    parity = {}
-    for m in ROWS:
-        ref = oracle.apply(m, U32, Xs, sign=s, d=d32)
-        got = Ys[m][idx].double().cpu().numpy()
-        parity[m] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-
+    parity = {r.name: r.parity() for r in rows}
     for _ in range(args.warmup):
-        for m in ROWS:
-            fns[m](X, out=Ys[m])
+        for r in rows:
+            r.run()
     torch.cuda.synchronize()
 
-    ev = {m: [] for m in ROWS}
-    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
-                           else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    ev = {r.name: [] for r in rows}
+    gpu_index = local
+    if "CUDA_VISIBLE_DEVICES" in os.environ:
+        try:
+            gpu_index = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+        except ValueError:
+            pass
+    sampler = ClockSampler(gpu_index)
     sampler.start()
     time.sleep(0.3)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
     for _ in range(args.steps):
-        for m in ROWS:
+        for r in rows:
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            fns[m](X, out=Ys[m])
+            r.run()
             b.record(stream)
-            ev[m].append((a, b))
-    t_end.record(stream)
+            ev[r.name].append((a, b))
+    t1.record(stream)
     torch.cuda.synchronize()
-    plan.sync()  # raises if any kernel in the timed region gave up a bounded wait
+    for r in rows:
+        r.plan.sync()  # raises if a kernel in the timed region gave up a bounded wait
     if pg:
         pg.barrier()
     clocks = sampler.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    ms_step = total_ms / args.steps
+    ms_step = t0.elapsed_time(t1) / args.steps
     if pg:
         t = torch.tensor([ms_step], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms_step = float(t.item())
-    kernel_ms = {m: statistics.mean(a.elapsed_time(b) for a, b in ev[m]) for m in ROWS}
-    value = world * B / (ms_step / 1e3)
+    vec_per_step = sum(r.vectors() for r in rows)
+    value = world * vec_per_step / (ms_step / 1e3)
 
-    peaks, peak_src = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # TFLOP/s
-    ridge = fp32_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
-    rows = {}
-    for m in ROWS:
-        by, fl = algorithmic(m, n, h, B)
-        t = kernel_ms[m] / 1e3
-        gbs = by / t / 1e9
-        tfl = fl / t / 1e12
-        rows[m] = {"ms": kernel_ms[m], "vectors_per_s": B / t, "GB_s": gbs,
-                   "dram_traffic_bytes": profiled_traffic(m, B),
-                   "hbm_frac": gbs / peaks["hbm_gbs"], "TFLOP_s": tfl, "alu_frac": tfl / fp32_peak,
-                   "intensity_flop_per_byte": fl / by, "bound": "hbm" if fl / by < ridge else "alu",
-                   "rel_l2_vs_oracle": parity[m]}
-    dom = max(ROWS, key=lambda m: kernel_ms[m])
-    r = rows[dom]
-    if r["bound"] == "hbm":
-        roof = {"bound": "hbm", "achieved": r["GB_s"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": r["hbm_frac"], "traffic": profiled_traffic(dom, B),
-                "kernel": f"staged_chain_kernel mode {dom}", "peak_source": f"hbm_gbs {peak_src}"}
-    else:
-        roof = {"bound": "alu", "achieved": r["TFLOP_s"], "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": r["alu_frac"], "traffic": profiled_traffic(dom, B),
-                "kernel": f"staged_chain_kernel mode {dom}",
-                "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x "
-                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (sm_max_mhz {peak_src})"}
+    peaks, psrc = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
+    peak_of = {"hbm": peaks["hbm_gbs"], "alu": fp32_peak, "tensor": bf16_peak}
+    out_rows = {}
+    for r in rows:
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev[r.name])
+        s = ms / 1e3
+        gbs, tfl = r.bytes() / s / 1e9, r.flops() / s / 1e12
+        ach = gbs if r.bound == "hbm" else tfl
+        traffic = (profiled_traffic(r.mode, r.vectors()) if isinstance(r, ChainRow) else None)
+        out_rows[r.name] = {"ms": ms, "vectors_per_s": r.vectors() / s, "GB_s": gbs,
+                            "TFLOP_s": tfl, "bound": r.bound, "frac": ach / peak_of[r.bound],
+                            "hbm_frac": gbs / peaks["hbm_gbs"], "launches": r.launches,
+                            "rel_l2_vs_oracle": parity[r.name], "dram_traffic_bytes": traffic}
+    dom = max(rows, key=lambda r: out_rows[r.name]["ms"])
+    d = out_rows[dom.name]
+    psource = {"hbm": f"hbm_gbs {psrc}",
+               "alu": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flops x "
+                      f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (sm_max_mhz {psrc})",
+               "tensor": f"bf16_tflops_sustained {psrc} (kernel timed inside a long step)"}
+    roof = {"bound": dom.bound, "achieved": d["GB_s"] if dom.bound == "hbm" else d["TFLOP_s"],
+            "peak": peak_of[dom.bound], "unit": "GB/s" if dom.bound == "hbm" else "TFLOP/s",
+            "frac": d["frac"], "traffic": d["dram_traffic_bytes"], "kernel": dom.name,
+            "peak_source": psource[dom.bound]}
+
+    compare = None
+    if not args.no_compare and any(isinstance(r, WYRow) for r in rows):
+        compare = compare_fp32(torch, dev, [r for r in rows if isinstance(r, WYRow)], out_rows)
 
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(torch, fns, X, B, n, dev, stream, world, pg, steps=max(3, min(args.steps, 10)))
+        e2e = measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        threads = oracle.max_threads()
-        rate, count, secs = oracle_sample_rate(WORKLOAD, ROWS, budget_s=12.0)
-        cpu = {"value": rate, "unit": "vectors/s", "cores": threads, "kind": "oracle",
-               "sample": f"{count} vectors (FP64, W + W^T + S each) in {secs:.1f} s"}
+        rates, _ = oracle_rates(names, budget_s=2.0)
+        full = step_vectors(names)
+        step_s = sum(full[nm] * t / c for nm, (c, t) in rates.items())
+        cpu = {"value": vec_per_step / step_s, "unit": "vectors/s", "cores": oracle.max_threads(),
+               "kind": "oracle",
+               "sample": "; ".join(f"{k}: {c} units in {t:.2f} s" for k, (c, t) in rates.items())
+                         + " (the full step's time extrapolated from each row's per-unit time)"}
 
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (Gaussian vectors and reflectors, seeded)", "config": config_dict(),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * len(ROWS), "clocks": clocks, "rows": rows,
-            "fp32_peak_tflops": fp32_peak,
-        }
+        line = {"metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (chain, distance, adjoint); bf16 storage with f32 accumulation (WY)",
+                "data": "synthetic (seeded Gaussian vectors, reflectors and mixture)",
+                "config": config_dict(names), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * sum(r.launches for r in rows), "clocks": clocks,
+                "rows": out_rows, "bf16_wy_vs_fp32_chain": compare,
+                "fp32_peak_tflops": fp32_peak}
         print(json.dumps(line))
     if pg:
         pg.destroy_process_group()
     return 0
 
 
-def measure_e2e(torch, fns, X, B, n, dev, stream, world, pg, steps):
-    """Same step through the public API from pinned host memory, results read back."""
-    Xh = torch.empty((B, n), dtype=torch.float32, pin_memory=True)
-    Xh.copy_(X.cpu())
-    Yh = torch.empty((B, n), dtype=torch.float32, pin_memory=True)
-    Xd = torch.empty_like(X)
-    Yd = torch.empty_like(X)
+def compare_fp32(torch, dev, wy_rows, out_rows):
+    """The FP32 chain on the WY rows' shapes and data: time and error vs the oracle."""
+    from paper_1811_07624_gb300 import Plan
+    import oracle
+
+    out = {}
+    for r in wy_rows:
+        pf = Plan(torch.tensor(r.U, device=dev, dtype=torch.float32))
+        X32 = r.X.float()
+        Y32 = torch.empty_like(X32)
+        for _ in range(2):
+            pf.apply(X32, out=Y32)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            pf.apply(X32, out=Y32)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 3
+        idx = torch.linspace(0, r.B - 1, 32, device=dev).long()
+        ref = oracle.apply("W", r.U, r.X[idx].double().cpu().numpy())
+        out[r.name] = {"fp32_chain_ms": ms, "bf16_wy_ms": out_rows[r.name]["ms"],
+                       "speedup": ms / out_rows[r.name]["ms"],
+                       "fp32_chain_rel_l2": rel_l2(Y32[idx].double().cpu().numpy(), ref),
+                       "bf16_wy_rel_l2": rel_l2(r.Y[idx].double().cpu().numpy(), ref),
+                       "errors_vs": "FP64 oracle on the unrounded reflectors and the BF16 inputs"}
+        del pf, X32, Y32
+    return out
+
+
+def measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step, steps=3):
+    """The step through the public API from pinned host memory, results read back."""
+    parts = [r.e2e(torch) for r in rows]
+    h2d = sum(p[0] for p in parts)
+    d2h = sum(p[1] for p in parts)
 
     def step():
-        Xd.copy_(Xh, non_blocking=True)
-        for m in ROWS:
-            fns[m](Xd, out=Yd)
-            Yh.copy_(Yd, non_blocking=True)
+        for p in parts:
+            p[2]()
 
     step()
     torch.cuda.synchronize()
@@ -412,10 +750,8 @@ def measure_e2e(torch, fns, X, B, n, dev, stream, world, pg, steps):
         t = torch.tensor([ms], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
-    nbytes = B * n * 4
-    return {"value": world * B / (ms / 1e3), "unit": "vectors/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes * len(ROWS),
-            "steps": steps}
+    return {"value": world * vec_per_step / (ms / 1e3), "unit": "vectors/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
 
 
 if __name__ == "__main__":
