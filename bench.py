@@ -9,12 +9,16 @@ synthetic vectors (inputs larger than L2, so no flush is needed):
   mahalanobis                    FP32 fast Mahalanobis distance, n=256, h=16, 1,048,576 pairs
   mahalanobis_grad               its gradient w.r.t. U and d (metric-learning loss)
   adjoint_SYM                    FP32 forward + adjoint of S x, n=1024, h=32, 65,536 vectors
+  batched_C5                     512 independent FP32 transforms, n in {128..2048}, h in
+                                 [4, 64], 1,024-16,384 vectors each, y = W x, in ONE
+                                 persistent graph-replayed launch (autotuned tile shapes)
 
 `value` is vectors per second through the whole step (the sum of the rows'
 vectors over the step time), timed with CUDA events on the launching stream.
 Each row also reports its own time, vectors/s, algorithmic GB/s and FLOP/s
 and roofline fraction; the FP32 chain on the WY rows' shapes and data is
-timed beside them ("BF16-WY vs FP32 plain").  `--impl reference` times the
+timed beside them ("BF16-WY vs FP32 plain"), and the 512 transforms of
+batched_C5 are also timed as 512 separate launches ("batched_vs_separate").  `--impl reference` times the
 FP64 CPU oracle on a bounded sample of the same rows.
 
     python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--gpus N]
@@ -44,8 +48,10 @@ N_CHAIN, H_CHAIN, B_CHAIN = 4096, 16, 262_144
 B_WY = 262_144
 N_MAHAL, H_MAHAL, P_MAHAL, PTS_MAHAL = 256, 16, 1 << 20, 100_000
 N_ADJ, H_ADJ, B_ADJ = 1024, 32, 65_536
+C5_COUNT, C5_SCALE = 512, 1.0
+C5_TUNE_H, C5_TUNE_ROWS = [4, 8, 16, 32, 64], 32_768
 ALL_ROWS = ["chain_W", "chain_WT", "chain_SYM", "wy_h64", "wy_h256", "wy_h1024", "mahalanobis",
-            "mahalanobis_grad", "adjoint_SYM"]
+            "mahalanobis_grad", "adjoint_SYM", "batched_C5"]
 
 KERNEL_SOURCES = ["paper_1811_07624_gb300/csrc/hh_staged.cuh",
                   "paper_1811_07624_gb300/csrc/hh_fused_f32.cu",
@@ -398,6 +404,130 @@ class AdjointRow:
         return (Xh.numel() + Gh.numel()) * 4, gUh.numel() * 4, step
 
 
+def c5_specs():
+    """The 512 transforms: (n, h, batch, seed), batches scaled by --batch-scale."""
+    import synthetic_inputs as si
+
+    return [(t["n"], t["h"], max(1, int(t["batch"] * C5_SCALE)), t["seed"])
+            for t in si.ragged_transforms(C5_COUNT)]
+
+
+class BatchedRow:
+    """512 ragged transforms (y = W x, FP32) in one graph-replayed persistent launch."""
+
+    def __init__(self, torch, dev):
+        import synthetic_inputs as si
+        import paper_1811_07624_gb300 as hh
+
+        self.name, self.torch = "batched_C5", torch
+        self.specs = c5_specs()
+        ns = sorted({n for n, _, _, _ in self.specs})
+        t0 = time.perf_counter()
+        hh.tune_clear()
+        hh.tune(ns, C5_TUNE_H, rows=C5_TUNE_ROWS)
+        self.tune_s = time.perf_counter() - t0
+        self.U = [si.reflectors(n, h, seed=sd) for n, h, _, sd in self.specs]
+        self.plans = [hh.Plan(torch.tensor(U, device=dev, dtype=torch.float32)) for U in self.U]
+        self.batch = hh.Batch(self.plans, [b for _, _, b, _ in self.specs])
+        self.plan = self.batch  # sync() after the timed region
+        total = sum(n * b for n, _, b, _ in self.specs)
+        g = torch.Generator(device=dev).manual_seed(77)
+        self.Xbuf = torch.randn(total, device=dev, generator=g)
+        self.Ybuf = torch.empty_like(self.Xbuf)
+        self.Xs, self.Ys, off = [], [], 0
+        for n, _, b, _ in self.specs:
+            self.Xs.append(self.Xbuf[off:off + n * b].view(b, n))
+            self.Ys.append(self.Ybuf[off:off + n * b].view(b, n))
+            off += n * b
+        self.launches = 1
+        self.bound = "hbm" if self.flops() / self.bytes() < 11.9 else "alu"
+        info = self.batch.info()
+        shapes = hh.batch_shapes()
+        self.info = {"items": info["items"], "grid": info["grid"], "tune_s": self.tune_s,
+                     "shape_use": {f"G{shapes[k]['G']}xNG{shapes[k]['NG']}xRT{shapes[k]['RT']}":
+                                   info["shapes"].count(k) for k in sorted(set(info["shapes"]))}}
+
+    def vectors(self):
+        return sum(b for _, _, b, _ in self.specs)
+
+    def bytes(self):
+        return float(sum(8 * n * b + 4 * n * h for n, h, b, _ in self.specs))
+
+    def flops(self):
+        return float(sum(4 * n * h * b for n, h, b, _ in self.specs))
+
+    def run(self):
+        self.batch.apply(self.Xs, self.Ys, mode="W")
+
+    def parity(self):
+        """Every transform on a 64-vector subset against the oracle; the worst error."""
+        import oracle
+
+        t = self.torch
+        worst = 0.0
+        for U, X, Y in zip(self.U, self.Xs, self.Ys):
+            idx = t.linspace(0, X.shape[0] - 1, min(64, X.shape[0]), device=X.device).long()
+            U32 = t.tensor(U, dtype=t.float32).double().numpy()
+            ref = oracle.apply("W", U32, X[idx].double().cpu().numpy())
+            worst = max(worst, rel_l2(Y[idx].double().cpu().numpy(), ref))
+        return worst
+
+    def separate(self):
+        """The same transforms as 512 hh_apply calls: issued from Python one by one,
+        and the same calls captured in one CUDA graph."""
+        t = self.torch
+        Ys = [t.empty_like(X) for X in self.Xs]
+
+        def all_apply():
+            for p, X, Y in zip(self.plans, self.Xs, Ys):
+                p.apply(X, out=Y)
+
+        def timed(fn, reps=3):
+            fn()
+            t.cuda.synchronize()
+            a, b = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            t.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        ms_loop = timed(all_apply)
+        s = t.cuda.Stream()
+        s.wait_stream(t.cuda.current_stream())
+        with t.cuda.stream(s):
+            all_apply()
+        t.cuda.current_stream().wait_stream(s)
+        t.cuda.synchronize()
+        graph = t.cuda.CUDAGraph()
+        with t.cuda.graph(graph, capture_error_mode="relaxed"):
+            all_apply()
+        ms_graph = timed(graph.replay)
+        same = max(rel_l2(a[:8].double().cpu().numpy(), b[:8].double().cpu().numpy())
+                   for a, b in zip(Ys, self.Ys))
+        del graph, Ys
+        return {"separate_launches_ms": ms_loop, "separate_launches_graph_ms": ms_graph,
+                "max_rel_diff_vs_batched": same}
+
+    def e2e(self, torch):
+        Xh = torch.empty(self.Xbuf.shape, dtype=self.Xbuf.dtype, pin_memory=True)
+        Xh.copy_(self.Xbuf)
+        Yh = torch.empty(self.Ybuf.shape, dtype=self.Ybuf.dtype, pin_memory=True)
+        Xd, Yd = torch.empty_like(self.Xbuf), torch.empty_like(self.Ybuf)
+        Xs, Ys, off = [], [], 0
+        for n, _, b, _ in self.specs:
+            Xs.append(Xd[off:off + n * b].view(b, n))
+            Ys.append(Yd[off:off + n * b].view(b, n))
+            off += n * b
+
+        def step():
+            Xd.copy_(Xh, non_blocking=True)
+            self.batch.apply(Xs, Ys, mode="W")
+            Yh.copy_(Yd, non_blocking=True)
+        return Xh.numel() * 4, Yh.numel() * 4, step
+
+
 def make_rows(torch, dev, names):
     rows = []
     for nm in names:
@@ -411,15 +541,18 @@ def make_rows(torch, dev, names):
             rows.append(MahalanobisRow(torch, dev, grad=True))
         elif nm == "adjoint_SYM":
             rows.append(AdjointRow(torch, dev))
+        elif nm == "batched_C5":
+            rows.append(BatchedRow(torch, dev))
         else:
             raise ValueError(f"unknown row {nm}")
     return rows
 
 
 def scale_batches(f):
-    global B_CHAIN, B_WY, P_MAHAL, B_ADJ
+    global B_CHAIN, B_WY, P_MAHAL, B_ADJ, C5_SCALE
     B_CHAIN, B_WY = max(1, int(B_CHAIN * f)), max(1, int(B_WY * f))
     P_MAHAL, B_ADJ = max(1, int(P_MAHAL * f)), max(1, int(B_ADJ * f))
+    C5_SCALE = f
 
 
 def config_dict(names):
@@ -427,7 +560,8 @@ def config_dict(names):
                         f"n={N_CHAIN} h={H_CHAIN} batch={B_CHAIN} (W, W^T, S); BF16 compact-WY "
                         f"n={N_CHAIN} h=64/256/1024 batch={B_WY} (W); fast Mahalanobis n={N_MAHAL} "
                         f"h={H_MAHAL} {P_MAHAL} pairs (+ gradient); adjoint of S n={N_ADJ} "
-                        f"h={H_ADJ} batch={B_ADJ}",
+                        f"h={H_ADJ} batch={B_ADJ}; {C5_COUNT} ragged FP32 transforms (n 128-2048, "
+                        f"h 4-64, batch 1024-16384 x {C5_SCALE:g}) in one batched launch",
             "rows": list(names), "l2": "every row's inputs are larger than L2 (no flush)",
             "parallelism": "replicas (one independent copy per rank)"}
 
@@ -471,6 +605,18 @@ def oracle_units(names):
                     sel = np.arange(c) % ia.shape[0]
                     oracle.mahalanobis(U, X, ia[sel], ib[sel], d)
             fns[nm] = f
+        elif nm == "batched_C5":
+            specs = c5_specs()
+            Us = [si.reflectors(n, h, seed=sd) for n, h, _, sd in specs]
+            pools = [si.vectors(16, n, seed=sd + 1) for n, _, _, sd in specs]
+            wts = np.array([b for _, _, b, _ in specs], dtype=np.float64)
+            wts /= wts.sum()
+
+            def f(c, Us=Us, pools=pools, wts=wts):
+                # c vectors spread over the transforms in proportion to their batches
+                for U, P, k in zip(Us, pools, np.maximum(1, np.floor(c * wts)).astype(int)):
+                    oracle.apply("W", U, np.resize(P, (k, P.shape[1])))
+            fns[nm] = f
         elif nm == "adjoint_SYM":
             U, d = si.reflectors(N_ADJ, H_ADJ, seed=9), si.spectrum(N_ADJ, seed=9)
             Xs, Gs = si.vectors(256, N_ADJ, seed=125), si.vectors(256, N_ADJ, seed=126)
@@ -500,6 +646,8 @@ def oracle_rates(names, budget_s):
 
 def step_vectors(names):
     per = {"chain": B_CHAIN, "wy": B_WY, "mahalanobis": P_MAHAL, "adjoint": B_ADJ}
+    if "batched_C5" in names:
+        per["batched"] = sum(b for _, _, b, _ in c5_specs())
     return {nm: per[nm.split("_")[0]] for nm in names}
 
 
@@ -661,6 +809,17 @@ def main():
     compare = None
     if not args.no_compare and any(isinstance(r, WYRow) for r in rows):
         compare = compare_fp32(torch, dev, [r for r in rows if isinstance(r, WYRow)], out_rows)
+    batched_vs = None
+    for r in rows:
+        if isinstance(r, BatchedRow):
+            out_rows[r.name].update(r.info)
+            if not args.no_compare:
+                batched_vs = r.separate()
+                batched_vs["batched_ms"] = out_rows[r.name]["ms"]
+                batched_vs["speedup_vs_separate"] = (batched_vs["separate_launches_ms"]
+                                                     / out_rows[r.name]["ms"])
+                batched_vs["speedup_vs_separate_graph"] = (batched_vs["separate_launches_graph_ms"]
+                                                           / out_rows[r.name]["ms"])
 
     e2e = None
     if not args.no_e2e:
@@ -685,6 +844,7 @@ def main():
                 "config": config_dict(names), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * sum(r.launches for r in rows), "clocks": clocks,
                 "rows": out_rows, "bf16_wy_vs_fp32_chain": compare,
+                "batched_vs_separate": batched_vs,
                 "fp32_peak_tflops": fp32_peak}
         print(json.dumps(line))
     if pg:

@@ -195,6 +195,76 @@ hh_status hh_mahalanobis_backward(hh_plan_t plan, const void *X, int64_t ldx, in
                                   const int64_t *ia, const int64_t *ib, int64_t npairs,
                                   const void *gout, void *gU, void *gd, void *stream);
 
+/*
+ * Batched persistent launch.  Many independent transforms (plans of uneven n
+ * and h, each with its own batch of vectors) applied in ONE persistent kernel
+ * launch, replayed from a CUDA graph.  The paper applies one transform at a
+ * time (§II-A); running many at once is this library's own addition, and so is
+ * the tile-shape autotuner below.
+ *
+ * hh_batch_create: plans[i] (count entries) must be F32 FUSED-path plans of
+ * the current device with n % 4 == 0 and n <= 4096 (else HH_ERR_UNSUPPORTED);
+ * batch[i] >= 0 is the number of vectors of transform i.  The batch refers to
+ * the plans, which must outlive it.  Tile shapes come from the autotuner's
+ * table (hh_tune / hh_tune_load / hh_tune_set) as it stands at create time.
+ * Allocates the work list and task table on the device; synchronous.
+ */
+typedef struct hh_batch_s *hh_batch_t;
+hh_status hh_batch_create(hh_batch_t *out, int count, const hh_plan_t *plans,
+                          const int64_t *batch);
+
+/*
+ * Apply every transform of the batch in `mode` (W, WT or SYM as hh_apply,
+ * hh_apply_T, hh_apply_sym): Y[i] = op_i(X[i]) for batch[i] rows.  X, Y: host
+ * arrays of count device pointers (16-byte aligned, rows of n floats);
+ * ldx, ldy: host arrays of count row strides (multiples of 4, >= n), or NULL
+ * for n.  X[i] == Y[i] is allowed with equal strides.  The first call per mode
+ * captures the launch (a counter reset and the kernel) in a CUDA graph; every
+ * call replays it on `stream`.  When the pointers or strides differ from the
+ * previous call, the task table is first copied to the device on `stream`.
+ * Stream-ordered; calls on different streams must not overlap on the GPU
+ * (they share the work counter).
+ */
+hh_status hh_batch_apply(hh_batch_t batch, hh_mode mode, const void *const *X, const int64_t *ldx,
+                         void *const *Y, const int64_t *ldy, void *stream);
+
+/* Report (and clear) the batch's device status word, as hh_sync.  Synchronises
+ * `stream`. */
+hh_status hh_batch_sync(hh_batch_t batch, void *stream);
+
+/* Work-list size, grid size, and the tile shape of each transform (count ints,
+ * or NULL). */
+hh_status hh_batch_info(hh_batch_t batch, int64_t *nitems, int *grid, int *shapes);
+
+/* Synchronises the device, then frees the batch.  NULL is a no-op. */
+hh_status hh_batch_destroy(hh_batch_t batch);
+
+/* Tile shapes of the batched kernel, 0 .. hh_batch_num_shapes()-1: G threads
+ * per row group, NG granules of 4 floats and RT rows per thread, rows per tile,
+ * and the largest n the shape covers (G * NG * 4). */
+int hh_batch_num_shapes(void);
+hh_status hh_batch_shape(int shape, int *G, int *NG, int *RT, int *rows_per_tile, int *cover);
+
+/*
+ * Autotuner.  hh_tune times, for every (n, h) in ns x hs, each tile shape that
+ * covers n on `rows` synthetic vectors (a batch of one transform, mode W,
+ * CUDA events on `stream`, 2 warm-up and 5 timed launches) and records the
+ * fastest in a process-wide table.  Needs n % 4 == 0, 4 <= n <= 4096.
+ * Synchronises `stream`.  hh_tune_get returns the shape hh_batch_create would
+ * use for (n, h): the table entry, else the entry of the nearest h for the same
+ * n, else a fixed rule; and the measured milliseconds per shape (hh_batch_num_
+ * shapes() floats, NaN where not measured), or NULL.  hh_tune_set pins an
+ * entry.  hh_tune_save / hh_tune_load write / merge the table as text lines
+ * "n h shape".  hh_tune_clear empties it.  Host-only except hh_tune.
+ */
+hh_status hh_tune(const int64_t *ns, int nn, const int64_t *hs, int nh, int64_t rows,
+                  void *stream);
+hh_status hh_tune_get(int64_t n, int64_t h, int *shape, float *ms);
+hh_status hh_tune_set(int64_t n, int64_t h, int shape);
+hh_status hh_tune_save(const char *path);
+hh_status hh_tune_load(const char *path);
+hh_status hh_tune_clear(void);
+
 /* Message for the last failed call on this host thread ("" if none). */
 const char *hh_last_error(void);
 

@@ -60,7 +60,23 @@ SIGNATURES = {
     "hh_backward_noalloc": [vp, ip, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
     "hh_mahalanobis": [vp, vp, i64, i64, vp, vp, i64, vp, vp],
     "hh_mahalanobis_backward": [vp, vp, i64, i64, vp, vp, i64, vp, vp, vp, vp],
+    "hh_batch_create": [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(i64)],
+    "hh_batch_apply": [vp, ip, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(vp),
+                       ctypes.POINTER(i64), vp],
+    "hh_batch_sync": [vp, vp],
+    "hh_batch_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(ip), ctypes.POINTER(ip)],
+    "hh_batch_destroy": [vp],
+    "hh_batch_shape": [ip] + [ctypes.POINTER(ip)] * 5,
+    "hh_tune": [ctypes.POINTER(i64), ip, ctypes.POINTER(i64), ip, i64, vp],
+    "hh_tune_get": [i64, i64, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_float)],
+    "hh_tune_set": [i64, i64, ip],
+    "hh_tune_save": [ctypes.c_char_p],
+    "hh_tune_load": [ctypes.c_char_p],
+    "hh_tune_clear": [],
 }
+
+# Functions that return a plain value, not an hh_status.
+VALUE_FUNCTIONS = {"hh_batch_num_shapes": ([], ctypes.c_int)}
 
 
 def header_symbols() -> list[str]:
@@ -85,6 +101,10 @@ def lib():
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = ctypes.c_int
+            for name, (args, res) in VALUE_FUNCTIONS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
             L.hh_last_error.argtypes = []
             L.hh_last_error.restype = ctypes.c_char_p
             L.hh_version.argtypes = []

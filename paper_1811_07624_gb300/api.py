@@ -196,3 +196,131 @@ class Plan:
         if need_gU and self.h == 0:
             gU = torch.zeros((0, self.n), device=X.device, dtype=self.dtype)
         return gU, gd
+
+
+# -- batched persistent launch ------------------------------------------------------
+class Batch:
+    """Many transforms applied in one persistent, graph-replayed launch.
+
+    plans: F32 plans (n % 4 == 0, n <= 4096); batches: rows per plan.  The
+    tile shape of each transform comes from the autotuner's table at creation
+    (:func:`tune`, :func:`tune_load`, :func:`tune_set`).  The batch keeps its
+    plans alive.
+    """
+
+    def __init__(self, plans, batches):
+        self.plans = list(plans)
+        self.batches = [int(b) for b in batches]
+        if len(self.plans) != len(self.batches):
+            raise ValueError("plans and batches differ in length")
+        for p in self.plans:
+            if p.dtype != torch.float32:
+                raise ValueError("the batched launch takes float32 plans only")
+        count = len(self.plans)
+        hs = (ctypes.c_void_p * max(count, 1))(*[p.handle.value for p in self.plans])
+        bs = (ctypes.c_int64 * max(count, 1))(*self.batches)
+        self._h = ctypes.c_void_p()
+        _lib.call("hh_batch_create", ctypes.byref(self._h), count, hs, bs)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.call("hh_batch_destroy", self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def apply(self, Xs, Ys=None, mode: str = "W", stream=None):
+        """Ys[i] = op(Xs[i]) for every transform, op = W, WT or SYM; one launch."""
+        count = len(self.plans)
+        if len(Xs) != count:
+            raise ValueError(f"expected {count} inputs, got {len(Xs)}")
+        if Ys is None:
+            Ys = [torch.empty_like(X) for X in Xs]
+        if len(Ys) != count:
+            raise ValueError(f"expected {count} outputs, got {len(Ys)}")
+        # the marshalled pointer arrays are kept while the tensors' pointers,
+        # shapes and strides stay the same (the usual case: one set of buffers)
+        key = tuple((X.data_ptr(), tuple(X.shape), X.stride(), X.dtype, X.device,
+                     Y.data_ptr(), tuple(Y.shape), Y.stride(), Y.dtype, Y.device)
+                    for X, Y in zip(Xs, Ys))
+        cache = getattr(self, "_marshalled", None)
+        if cache is None or cache[0] != key:
+            xp, yp, lx, ly = [], [], [], []
+            for i, (p, X, Y, b) in enumerate(zip(self.plans, Xs, Ys, self.batches)):
+                if X.shape[0] != b or Y.shape[0] != b:
+                    raise ValueError(f"transform {i}: expected {b} rows")
+                a, la = _rows(X, f"Xs[{i}]", p.n, torch.float32)
+                c, lc = _rows(Y, f"Ys[{i}]", p.n, torch.float32)
+                xp.append(a)
+                yp.append(c)
+                lx.append(la)
+                ly.append(lc)
+            n = max(count, 1)
+            cache = (key, (ctypes.c_void_p * n)(*xp), (ctypes.c_int64 * n)(*lx),
+                     (ctypes.c_void_p * n)(*yp), (ctypes.c_int64 * n)(*ly))
+            self._marshalled = cache
+        _lib.call("hh_batch_apply", self._h, _lib.MODES[mode], cache[1], cache[2], cache[3],
+                  cache[4], _stream_ptr(stream))
+        return Ys
+
+    def sync(self, stream=None) -> None:
+        _lib.call("hh_batch_sync", self._h, _stream_ptr(stream))
+
+    def info(self) -> dict:
+        count = len(self.plans)
+        ni = ctypes.c_int64()
+        grid = ctypes.c_int()
+        shapes = (ctypes.c_int * max(count, 1))()
+        _lib.call("hh_batch_info", self._h, ctypes.byref(ni), ctypes.byref(grid), shapes)
+        return {"items": ni.value, "grid": grid.value, "shapes": list(shapes)[:count]}
+
+
+def batch_shapes() -> list[dict]:
+    """The tile shapes compiled into the batched kernel."""
+    out = []
+    for s in range(_lib.lib().hh_batch_num_shapes()):
+        v = [ctypes.c_int() for _ in range(5)]
+        _lib.call("hh_batch_shape", s, *[ctypes.byref(x) for x in v])
+        out.append(dict(zip(("G", "NG", "RT", "rows_per_tile", "cover"), [x.value for x in v])))
+    return out
+
+
+def tune(ns, hs, rows: int = 16384, stream=None) -> None:
+    """Time every tile shape for each (n, h) and keep the fastest (hh_tune)."""
+    ns, hs = [int(n) for n in ns], [int(h) for h in hs]
+    _lib.call("hh_tune", (ctypes.c_int64 * max(len(ns), 1))(*ns), len(ns),
+              (ctypes.c_int64 * max(len(hs), 1))(*hs), len(hs), int(rows), _stream_ptr(stream))
+
+
+def tune_get(n: int, h: int):
+    """(shape the batch would use for (n, h), measured ms per shape or NaN)."""
+    shape = ctypes.c_int()
+    ms = (ctypes.c_float * _lib.lib().hh_batch_num_shapes())()
+    _lib.call("hh_tune_get", int(n), int(h), ctypes.byref(shape), ms)
+    return shape.value, list(ms)
+
+
+def tune_set(n: int, h: int, shape: int) -> None:
+    _lib.call("hh_tune_set", int(n), int(h), int(shape))
+
+
+def tune_save(path: str) -> None:
+    _lib.call("hh_tune_save", str(path).encode())
+
+
+def tune_load(path: str) -> None:
+    _lib.call("hh_tune_load", str(path).encode())
+
+
+def tune_clear() -> None:
+    _lib.call("hh_tune_clear")

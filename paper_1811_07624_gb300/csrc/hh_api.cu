@@ -30,7 +30,7 @@ hh_status cuda_fail(cudaError_t e, const char *what) {
 
 // A pointer the current device's kernels may dereference: device memory of the
 // current device, or managed memory.  Host and unregistered pointers are not.
-static bool device_ptr(const void *p, int dev) {
+bool device_ptr(const void *p, int dev) {
     if (!p) return false;
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -56,7 +56,7 @@ static void free_plan(Plan *p) {
     delete p;
 }
 
-static hh_status check_plan(const Plan *p) {
+hh_status check_plan(const Plan *p) {
     if (!p) return fail(HH_ERR_INVALID_ARG, "plan is NULL");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);

@@ -50,6 +50,11 @@ struct Plan {
 hh_status fail(hh_status st, const char *fmt, ...);
 hh_status cuda_fail(cudaError_t e, const char *what);
 
+// A pointer the kernels of device `dev` may dereference (device or managed memory).
+bool device_ptr(const void *p, int dev);
+// The plan is non-null and belongs to the current device.
+hh_status check_plan(const Plan *p);
+
 inline size_t dtype_size(hh_dtype t) {
     return t == HH_F64 ? 8 : (t == HH_BF16 ? 2 : 4);
 }

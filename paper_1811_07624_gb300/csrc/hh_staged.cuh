@@ -98,7 +98,6 @@ struct SCfg {
     static constexpr int L = 32 / NV;     // lanes holding one value after the warp reduction
     static constexpr bool KEEP = B * E <= 32;  // keep the block's reflector values in registers
     static_assert(G % 32 == 0, "G must be a multiple of 32");
-    static_assert(RG == 1 || NW == 1, "several row groups only with one warp each");
     static_assert(NV <= 32 && (NV & (NV - 1)) == 0, "B*RT must be a power of two <= 32");
     static_assert(B >= 1 && B <= kGramBand, "block larger than the stored Gram band");
 };
@@ -118,13 +117,33 @@ __device__ __forceinline__ void scale2(float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E
     }
 }
 
-// Apply h reflectors to the RT rows in x, ascending (k = 0..h-1) or descending
-// (k = h-1..0), in blocks of B.
+// Scale the columns of the held rows by s; with SKIP, only the first `act`
+// granule indices (warp-uniform) are touched.
 template <int G, int NG, int RT, int RG, int B>
+__device__ __forceinline__ void scale2_part(float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E2],
+                                            const float *__restrict__ s, int t, int act) {
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        if (i >= act) break;
+        float4 q = __ldg(reinterpret_cast<const float4 *>(s) + (t + G * i));
+        const float2 lo = make_float2(q.x, q.y), hi = make_float2(q.z, q.w);
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            x[r][2 * i] = __fmul2_rn(x[r][2 * i], lo);
+            x[r][2 * i + 1] = __fmul2_rn(x[r][2 * i + 1], hi);
+        }
+    }
+}
+
+// Apply h reflectors to the RT rows in x, ascending (k = 0..h-1) or descending
+// (k = h-1..0), in blocks of B.  With SKIP, granule indices i >= act (a
+// warp-uniform count: the warp's columns there lie past n) are neither read
+// nor computed.
+template <int G, int NG, int RT, int RG, int B, bool SKIP = false>
 __device__ __forceinline__ void chain(
     float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E2], bool asc, int h, const float *__restrict__ V,
     int64_t ldv, const float *__restrict__ tau, const float *__restrict__ gram, int t, int lane,
-    int warp, int rg, float *red, int &buf) {
+    int warp, int rg, float *red, int &buf, int act = NG) {
     using C = SCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L;
     for (int s = 0; s < h; s += B) {
@@ -144,7 +163,7 @@ __device__ __forceinline__ void chain(
 #pragma unroll
             for (int i = 0; i < NG; ++i) {
                 float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < nb)
+                if (j < nb && (!SKIP || i < act))
                     q = __ldg(reinterpret_cast<const float4 *>(V + (size_t)kk[j] * ldv) + (t + G * i));
                 dst[2 * i] = make_float2(q.x, q.y);
                 dst[2 * i + 1] = make_float2(q.z, q.w);
@@ -159,16 +178,35 @@ __device__ __forceinline__ void chain(
         for (int j = 0; j < B; ++j) {
             if constexpr (!C::KEEP) load_u(j, u[0]);
             const float2(&uj)[E2] = u[C::KEEP ? j : 0];
+            if constexpr (SKIP) {
+                // granule-major, so one warp-uniform test per granule; one
+                // packed accumulator per row
+                float2 a[RT];
 #pragma unroll
-            for (int r = 0; r < RT; ++r) {
-                float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+                for (int r = 0; r < RT; ++r) a[r] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int e = 0; e < E2; e += 2) {
-                    a = __ffma2_rn(x[r][e], uj[e], a);
-                    if (e + 1 < E2) b = __ffma2_rn(x[r][e + 1], uj[e + 1], b);
+                for (int i = 0; i < NG; ++i) {
+                    if (i >= act) break;
+#pragma unroll
+                    for (int r = 0; r < RT; ++r) {
+                        a[r] = __ffma2_rn(x[r][2 * i], uj[2 * i], a[r]);
+                        a[r] = __ffma2_rn(x[r][2 * i + 1], uj[2 * i + 1], a[r]);
+                    }
                 }
-                a = __fadd2_rn(a, b);
-                p[j * RT + r] = a.x + a.y;
+#pragma unroll
+                for (int r = 0; r < RT; ++r) p[j * RT + r] = a[r].x + a[r].y;
+            } else {
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int e = 0; e < E2; e += 2) {
+                        a = __ffma2_rn(x[r][e], uj[e], a);
+                        if (e + 1 < E2) b = __ffma2_rn(x[r][e + 1], uj[e + 1], b);
+                    }
+                    a = __fadd2_rn(a, b);
+                    p[j * RT + r] = a.x + a.y;
+                }
             }
         }
         float v = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
@@ -214,11 +252,24 @@ __device__ __forceinline__ void chain(
         for (int j = 0; j < B; ++j) {
             if constexpr (!C::KEEP) load_u(j, u[0]);
             const float2(&uj)[E2] = u[C::KEEP ? j : 0];
+            if constexpr (SKIP) {
 #pragma unroll
-            for (int r = 0; r < RT; ++r) {
-                const float2 cc = make_float2(c[j][r], c[j][r]);
+                for (int i = 0; i < NG; ++i) {
+                    if (i >= act) break;
 #pragma unroll
-                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
+                    for (int r = 0; r < RT; ++r) {
+                        const float2 cc = make_float2(c[j][r], c[j][r]);
+                        x[r][2 * i] = __ffma2_rn(uj[2 * i], cc, x[r][2 * i]);
+                        x[r][2 * i + 1] = __ffma2_rn(uj[2 * i + 1], cc, x[r][2 * i + 1]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    const float2 cc = make_float2(c[j][r], c[j][r]);
+#pragma unroll
+                    for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
+                }
             }
         }
     }

@@ -6,6 +6,7 @@ import ctypes
 
 import pytest
 
+import paper_1811_07624_gb300 as hh
 from paper_1811_07624_gb300 import _lib
 from paper_1811_07624_gb300.build import build_library
 
@@ -27,7 +28,8 @@ def test_signatures_cover_header(L):
     for name in _lib.header_symbols():
         if name in ("hh_last_error", "hh_version"):
             continue
-        assert name in _lib.SIGNATURES, f"no ctypes signature for {name}"
+        assert name in _lib.SIGNATURES or name in _lib.VALUE_FUNCTIONS, \
+            f"no ctypes signature for {name}"
 
 
 def test_version_and_errors_without_device(L):
@@ -52,3 +54,64 @@ def test_python_error_type(L):
     with pytest.raises(_lib.HHError) as ei:
         _lib.call("hh_plan_info", None, None, None, None, None)
     assert ei.value.code == "HH_ERR_INVALID_ARG"
+
+
+def test_batch_shapes_and_tune_table_without_device(L, tmp_path):
+    """The tile-shape table and the autotuner's table I/O are host logic."""
+    shapes = hh.batch_shapes()
+    assert len(shapes) == L.hh_batch_num_shapes() >= 2
+    for s in shapes:
+        assert s["cover"] == s["G"] * s["NG"] * 4
+        # every shape stages ROWS x COVER floats in 64 KB of shared memory
+        assert s["rows_per_tile"] * s["cover"] * 4 == 65536
+    covers = sorted({s["cover"] for s in shapes})
+    assert covers[-1] >= 4096
+    hh.tune_clear()
+    # untuned: the fixed rule, the smallest cover with four rows per thread
+    for n in (4, 128, 256, 260, 512, 1024, 2048, 4096):
+        shape, ms = hh.tune_get(n, 16)
+        assert shapes[shape]["cover"] >= n
+        assert all(m != m for m in ms)  # NaN: nothing measured
+    hh.tune_set(640, 8, 4)
+    hh.tune_set(640, 64, 5)
+    assert hh.tune_get(640, 8)[0] == 4
+    assert hh.tune_get(640, 64)[0] == 5
+    assert hh.tune_get(640, 10)[0] == 4   # nearest tuned h
+    assert hh.tune_get(640, 50)[0] == 5
+    path = tmp_path / "shapes.txt"
+    hh.tune_save(str(path))
+    lines = [ln for ln in path.read_text().splitlines() if not ln.startswith("#")]
+    assert sorted(lines) == ["640 64 5", "640 8 4"]
+    hh.tune_clear()
+    assert hh.tune_get(640, 8)[0] != 4 or shapes[4]["cover"] < 640
+    hh.tune_load(str(path))
+    assert hh.tune_get(640, 8)[0] == 4
+    # a shape that does not cover n is refused, in both routes
+    small = min(range(len(shapes)), key=lambda s: shapes[s]["cover"])
+    with pytest.raises(hh.HHError, match="INVALID_ARG"):
+        hh.tune_set(4096, 8, small)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("4096 8 %d\n" % small)
+    with pytest.raises(hh.HHError, match="INVALID_ARG"):
+        hh.tune_load(str(bad))
+    bad.write_text("128 x 0\n")
+    with pytest.raises(hh.HHError, match="INVALID_ARG"):
+        hh.tune_load(str(bad))
+    with pytest.raises(hh.HHError, match="INVALID_ARG"):
+        hh.tune_load(str(tmp_path / "missing.txt"))
+    hh.tune_clear()
+
+
+def test_batch_errors_without_device(L):
+    import ctypes
+    assert L.hh_batch_destroy(None) == 0
+    st = L.hh_batch_create(None, 0, None, None)
+    assert _lib.STATUS[st] == "HH_ERR_INVALID_ARG"
+    h = ctypes.c_void_p()
+    st = L.hh_batch_create(ctypes.byref(h), -1, None, None)
+    assert _lib.STATUS[st] == "HH_ERR_INVALID_ARG"
+    st = L.hh_batch_apply(None, 0, None, None, None, None, None)
+    assert _lib.STATUS[st] == "HH_ERR_INVALID_ARG"
+    assert _lib.STATUS[L.hh_batch_shape(-1, None, None, None, None, None)] == "HH_ERR_INVALID_ARG"
+    st = L.hh_tune(None, 1, None, 1, 16, None)
+    assert _lib.STATUS[st] == "HH_ERR_INVALID_ARG"
