@@ -18,13 +18,12 @@
 // orthogonality rests on).  The sign D of Eq. (1) is applied in the last
 // panel's epilogue (W) or folded into the first panel's V and epilogue (W^T).
 //
-// Kernel, per 128-row tile, one CTA of 4 warps: thread 0 issues the TMA loads
-// (128-byte swizzle) and the tcgen05 MMAs; GEMM 1 streams K in chunks of 64
-// through a 2-stage ring into tensor memory; the warps move Z (FP32) to shared
-// memory as BF16 in the operand layout; GEMM 2 runs over N in chunks of 128
-// with two tensor-memory accumulators, so the MMAs of chunk c+1 overlap the
-// epilogue of chunk c (y = x - acc, read from tensor memory by the warp that
-// owns the row).  All mbarrier waits are bounded.
+// Kernel: persistent, one CTA per SM over 128-row tiles, warp-specialised (a
+// TMA warp, an MMA warp, four epilogue warps), operands in a ring of TMA
+// stages (128-byte swizzle), GEMM 2 in 64-column chunks over four tensor-memory
+// accumulators so the epilogue of one chunk overlaps the MMAs of the next and
+// GEMM 1 of the next tile; details at wy_panel_kernel.  All mbarrier waits are
+// bounded.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -48,12 +47,15 @@ struct WYPlan {
 
 namespace wy {
 
-constexpr int kTileM = 128;
-constexpr int kChunkN = 128;
-constexpr int kThreads = 128;
-constexpr size_t kStageBytes = 64 * 1024;  // ring stage: max(A 16 KB + B PB*128 B, PB*256 B)
-constexpr size_t kZBytes = 64 * 1024;      // 128 x 256 BF16
-constexpr size_t kSmemBytes = 1024 + 2 * kStageBytes + kZBytes;
+constexpr int kTileM = 128;     // rows per tile (M of both GEMMs)
+constexpr int kChunkN = 64;     // output columns per GEMM 2 accumulator
+constexpr int kNumAcc = 4;      // accumulators, tensor-memory columns 256 + 64a
+constexpr int kThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kMaxStages = 8;
+constexpr uint32_t kEBox = kTileM * kChunkN * 2;  // epilogue box, 128 x 64 BF16 = 16 KB
+// Dynamic shared memory: 1 KB alignment slack, Z (PB x 256 B), the epilogue
+// ring and the operand ring; sized per plan by the host (panel_layout).
+constexpr size_t kSmemBytes = 220 * 1024;
 
 // ---- create-time kernels (FP64) ---------------------------------------------------------
 
@@ -160,12 +162,10 @@ wy_vprime_kernel(const double *__restrict__ V64, const double *__restrict__ T, i
 // ---- the apply kernel -----------------------------------------------------------------------
 
 struct PanelArgs {
-    const __nv_bfloat16 *Xin;   // panel input (epilogue reads x here)
-    int64_t ldx;
-    __nv_bfloat16 *Y;
-    int64_t ldy;
-    int64_t batch;
+    int64_t tiles;
     int n, PB, panel;
+    int stages;         // operand ring stages of 16 KB + PB x 128 B
+    int estages;        // epilogue ring stages of 16 KB (128 rows x 64 columns)
     const float *sign;  // applied per the flags, or null
     int sign_out;       // y = sigma .* (x - acc)  (W, last panel)
     int sign_in;        // y = sigma .* x - acc    (W^T, first panel; GEMM 1 uses the scaled V)
@@ -177,203 +177,266 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
+// Shared state of the persistent panel kernel.
+struct Bars {
+    uint64_t full[kMaxStages], empty[kMaxStages];    // operand ring
+    uint64_t efull[kMaxStages], eempty[kMaxStages];  // epilogue ring (x in, y out)
+    uint64_t z_full, z_free;                         // Z in tensor memory: written / drained
+    uint64_t zs_full, zs_free;                       // Z as BF16 operand in shared memory
+    uint64_t acc_full[kNumAcc], acc_empty[kNumAcc];
+    uint32_t tbase;
+    int aborted;
+};
+
+// Persistent, warp-specialised panel kernel: one CTA per SM walks 128-row
+// tiles.  Shared memory: Z as GEMM 2's BF16 operand (128 x PB), an epilogue ring
+// of 128 x 64 boxes of X (y is written over x and stored from there), and an
+// operand ring.  Warp 0 (one thread) issues every TMA load, in the order the
+// consumers need them: per tile the K chunks of GEMM 1 (an X box and a V box),
+// then per output chunk a V' box set (GEMM 2) and an X box (epilogue).  Warp 1
+// (one thread) issues the MMAs: GEMM 1 into Z (tensor-memory columns [0, PB)),
+// then GEMM 2 per 64-column chunk into one of four accumulators (columns
+// 256 + 64a).  Warps 2..5 (one tensor-memory lane quadrant each, one row per
+// thread) move Z to shared memory, then per chunk compute y = x - acc in the
+// epilogue box; one thread stores the box by TMA.  GEMM 1 of the next tile
+// starts once Z has been moved.  Chunks run from the last column to the first,
+// so the X boxes GEMM 1 read last are read again first (more L2 hits).  TMA
+// zero-fills loads and clips stores at the tensor's edges (rows past the
+// batch, columns past n).
 __global__ void __launch_bounds__(kThreads, 1)
 wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapV,
-                const __grid_constant__ CUtensorMap mapVp, PanelArgs a) {
+                const __grid_constant__ CUtensorMap mapVp, const __grid_constant__ CUtensorMap mapY,
+                PanelArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *stage[2] = {smem, smem + kStageBytes};
-    unsigned char *Zs = smem + 2 * kStageBytes;
-    __shared__ __align__(8) uint64_t full[2], empty[2], zbar, accbar[2];
-    __shared__ uint32_t tbase;
-    __shared__ int aborted;
+    const int n = a.n, PB = a.PB, NS = a.stages, NE = a.estages;
+    unsigned char *Zs = smem;
+    unsigned char *ering = Zs + (size_t)PB * 256;
+    unsigned char *ring = ering + (size_t)NE * kEBox;
+    __shared__ Bars B;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n = a.n, PB = a.PB;
-    const int64_t row0 = (int64_t)blockIdx.x * kTileM;
     const int KC = (n + 63) / 64;
     const int NC = (n + kChunkN - 1) / kChunkN;
-    const uint32_t bytesA = kTileM * 128, bytesB1 = (uint32_t)PB * 128, bytesB2 = (uint32_t)PB * 256;
+    const uint32_t bytesX = kTileM * 128, bytesV = (uint32_t)PB * 128;
+    const uint32_t stage_bytes = bytesX + bytesV;
     const int ybase = a.panel * PB;  // first row of this panel in V
     const int vpbase = a.panel * n;  // first row of this panel in V' (P x n rows)
 
-    if (warp == 0) tc::tmem_alloc(&tbase, 512);
     if (tid == 0) {
-        aborted = 0;
-        for (int s = 0; s < 2; ++s) {
-            tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&empty[s], 1);
-            tc::mbar_init(&accbar[s], 1);
+        B.aborted = 0;
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&B.full[s], 1);
+            tc::mbar_init(&B.empty[s], 1);
         }
-        tc::mbar_init(&zbar, 1);
+        for (int s = 0; s < NE; ++s) {
+            tc::mbar_init(&B.efull[s], 1);
+            tc::mbar_init(&B.eempty[s], 1);
+        }
+        tc::mbar_init(&B.z_full, 1);
+        tc::mbar_init(&B.z_free, 4);
+        tc::mbar_init(&B.zs_full, 4);
+        tc::mbar_init(&B.zs_free, 1);
+        for (int c = 0; c < kNumAcc; ++c) {
+            tc::mbar_init(&B.acc_full[c], 1);
+            tc::mbar_init(&B.acc_empty[c], 4);
+        }
         tc::fence_barrier_init();
         tc::prefetch_tensormap(&mapX);
         tc::prefetch_tensormap(&mapV);
         tc::prefetch_tensormap(&mapVp);
+        tc::prefetch_tensormap(&mapY);
     }
+    if (warp == 1) tc::tmem_alloc(&B.tbase, 512);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const uint32_t tz = tbase;                 // Z: columns [0, PB)
-    const uint32_t tacc[2] = {tbase + 256, tbase + 384};
+    const uint32_t tz = B.tbase;
 
+    // Bounded wait; after a timeout the kernel records HH_ERR_TIMEOUT and stops
+    // waiting (its results are then not to be trusted).
     auto wait = [&](uint64_t *bar, uint32_t parity) {
-        if (*(volatile int *)&aborted) return;
+        if (*(volatile int *)&B.aborted) return;
         if (!tc::mbar_wait(bar, parity)) {
             atomicExch(a.err, (int)HH_ERR_TIMEOUT);
-            tc::mbar_wait(bar, parity);
-            *(volatile int *)&aborted = 1;
+            *(volatile int *)&B.aborted = 1;
         }
     };
 
-    // ---- GEMM 1: Z = X_tile V_panel^T over K = n -------------------------------------------
-    if (tid == 0) {
-        auto load1 = [&](int kc, int s) {
-            tc::mbar_expect_tx(&full[s], bytesA + bytesB1);
-            tc::tma_load_2d(stage[s], &mapX, kc * 64, (int)row0, &full[s]);
-            tc::tma_load_2d(stage[s] + bytesA, &mapV, kc * 64, ybase, &full[s]);
-        };
-        load1(0, 0);
-        if (KC > 1) load1(1, 1);
-        const uint32_t id1 = tc::idesc_bf16(kTileM, PB);
-        for (int kc = 0; kc < KC; ++kc) {
-            const int s = kc & 1;
-            wait(&full[s], (uint32_t)((kc >> 1) & 1));
+    if (warp == 0) {
+        // ---- TMA producer -------------------------------------------------------------------
+        if (lane == 0) {
+            uint32_t it = 0, ei = 0;
+            for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+                const int row0 = (int)(tile * kTileM);
+                for (int kc = 0; kc < KC; ++kc, ++it) {
+                    const uint32_t s = it % NS;
+                    wait(&B.empty[s], ((it / NS) & 1) ^ 1);
+                    unsigned char *st = ring + s * stage_bytes;
+                    tc::mbar_expect_tx(&B.full[s], bytesX + bytesV);
+                    tc::tma_load_2d(st, &mapX, kc * 64, row0, &B.full[s]);
+                    tc::tma_load_2d(st + bytesX, &mapV, kc * 64, ybase, &B.full[s]);
+                }
+                for (int j = 0; j < NC; ++j, ++it, ++ei) {
+                    const int nc = NC - 1 - j;
+                    const uint32_t s = it % NS;
+                    wait(&B.empty[s], ((it / NS) & 1) ^ 1);
+                    unsigned char *st = ring + s * stage_bytes;
+                    tc::mbar_expect_tx(&B.full[s], (uint32_t)PB * 128);
+                    for (int kb = 0; kb < PB / 64; ++kb)
+                        tc::tma_load_2d(st + kb * (kChunkN * 128), &mapVp, kb * 64,
+                                        vpbase + nc * kChunkN, &B.full[s]);
+                    const uint32_t e = ei % NE;
+                    wait(&B.eempty[e], ((ei / NE) & 1) ^ 1);
+                    tc::mbar_expect_tx(&B.efull[e], kEBox);
+                    tc::tma_load_2d(ering + e * kEBox, &mapX, nc * kChunkN, row0, &B.efull[e]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ---------------------------------------------------------------------
+        if (lane == 0) {
+            const uint32_t id1 = tc::idesc_bf16(kTileM, PB);
+            const uint32_t id2 = tc::idesc_bf16(kTileM, kChunkN);
+            const uint32_t sz = tc::smem_u32(Zs);
+            uint32_t it = 0, ai = 0, ti = 0;
+            for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++ti) {
+                wait(&B.z_free, (ti & 1) ^ 1);  // the epilogue has moved the previous Z
+                tc::tc_fence_after();
+                for (int kc = 0; kc < KC; ++kc, ++it) {
+                    const uint32_t s = it % NS;
+                    wait(&B.full[s], (it / NS) & 1);
+                    tc::tc_fence_after();
+                    const uint32_t sa = tc::smem_u32(ring + s * stage_bytes), sb = sa + bytesX;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tc::mma_bf16(tz, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k),
+                                     id1, (kc | k) != 0);
+                    tc::mma_commit(&B.empty[s]);
+                }
+                tc::mma_commit(&B.z_full);
+                wait(&B.zs_full, ti & 1);  // Z as BF16 operand is in shared memory
+                tc::tc_fence_after();
+                for (int j = 0; j < NC; ++j, ++it, ++ai) {
+                    const uint32_t c = ai % kNumAcc;
+                    wait(&B.acc_empty[c], ((ai / kNumAcc) & 1) ^ 1);
+                    const uint32_t s = it % NS;
+                    wait(&B.full[s], (it / NS) & 1);
+                    tc::tc_fence_after();
+                    const uint32_t sb = tc::smem_u32(ring + s * stage_bytes);
+                    const uint32_t tacc = tz + 256 + c * kChunkN;
+                    for (int k = 0; k < PB / 16; ++k) {
+                        const uint32_t offa = (uint32_t)(k >> 2) * (kTileM * 128) + (uint32_t)(k & 3) * 32;
+                        const uint32_t offb = (uint32_t)(k >> 2) * (kChunkN * 128) + (uint32_t)(k & 3) * 32;
+                        tc::mma_bf16(tacc, tc::sdesc_sw128(sz + offa), tc::sdesc_sw128(sb + offb), id2,
+                                     k != 0);
+                    }
+                    tc::mma_commit(&B.empty[s]);
+                    tc::mma_commit(&B.acc_full[c]);
+                }
+                tc::mma_commit(&B.zs_free);  // GEMM 2 of this tile has read Z
+            }
+            if (ti > 0) wait(&B.zs_free, (ti - 1) & 1);  // last commit landed before exit
+        }
+    } else {
+        // ---- epilogue: warps 2..5, tensor-memory lane quadrant warp % 4 ----------------------
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const bool leader = warp == 2 && lane == 0;  // stores the epilogue boxes
+        uint32_t ai = 0, ti = 0, ei = 0;
+        for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++ti) {
+            const int row0 = (int)(tile * kTileM);
+            wait(&B.z_full, ti & 1);
+            wait(&B.zs_free, (ti & 1) ^ 1);  // GEMM 2 of the previous tile has read Zs
             tc::tc_fence_after();
-            const uint32_t sa = tc::smem_u32(stage[s]), sb = sa + bytesA;
+            for (int c = 0; c < PB / 32; ++c) {
+                uint32_t r[32];
+                tc::tmem_ld32(tz + lane_off + (uint32_t)(c * 32), r);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                tc::mma_bf16(tz, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k), id1,
-                             (kc | k) != 0);
-            tc::mma_commit(&empty[s]);
-            if (kc + 2 < KC) {
-                wait(&empty[s], (uint32_t)((kc >> 1) & 1));
-                load1(kc + 2, s);
+                for (int qq = 0; qq < 4; ++qq) {
+                    uint4 w;
+                    w.x = pack_bf16(__uint_as_float(r[8 * qq + 0]), __uint_as_float(r[8 * qq + 1]));
+                    w.y = pack_bf16(__uint_as_float(r[8 * qq + 2]), __uint_as_float(r[8 * qq + 3]));
+                    w.z = pack_bf16(__uint_as_float(r[8 * qq + 4]), __uint_as_float(r[8 * qq + 5]));
+                    w.w = pack_bf16(__uint_as_float(r[8 * qq + 6]), __uint_as_float(r[8 * qq + 7]));
+                    *reinterpret_cast<uint4 *>(Zs + tc::sw128_offset(m, c * 32 + 8 * qq, kTileM)) = w;
+                }
+            }
+            tc::fence_proxy_async();
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(&B.zs_full);
+                tc::mbar_arrive(&B.z_free);
+            }
+            for (int j = 0; j < NC; ++j, ++ai, ++ei) {
+                const int nc = NC - 1 - j;
+                const uint32_t c = ai % kNumAcc;
+                const uint32_t e = ei % NE;
+                wait(&B.acc_full[c], (ai / kNumAcc) & 1);
+                tc::tc_fence_after();
+                uint32_t r[kChunkN];
+                tc::tmem_ld32(tz + lane_off + 256 + c * kChunkN, *reinterpret_cast<uint32_t(*)[32]>(r));
+                tc::tmem_ld32(tz + lane_off + 256 + c * kChunkN + 32,
+                              *reinterpret_cast<uint32_t(*)[32]>(r + 32));
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&B.acc_empty[c]);
+                wait(&B.efull[e], (ei / NE) & 1);
+                // row m of the box: 128 bytes, 16-byte granules permuted by the swizzle
+                unsigned char *box = ering + e * kEBox + m * 128;
+                const int col0 = nc * kChunkN;
+#pragma unroll
+                for (int q8 = 0; q8 < kChunkN / 8; ++q8) {
+                    uint4 *g = reinterpret_cast<uint4 *>(box + ((q8 ^ (m & 7)) << 4));
+                    const uint4 xv = *g;
+                    float sg[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+                    if (a.sign && col0 + 8 * q8 + 8 <= n) {
+                        const float4 s0 = *reinterpret_cast<const float4 *>(a.sign + col0 + 8 * q8);
+                        const float4 s1 = *reinterpret_cast<const float4 *>(a.sign + col0 + 8 * q8 + 4);
+                        sg[0] = s0.x; sg[1] = s0.y; sg[2] = s0.z; sg[3] = s0.w;
+                        sg[4] = s1.x; sg[5] = s1.y; sg[6] = s1.z; sg[7] = s1.w;
+                    }
+                    const uint32_t *xw = reinterpret_cast<const uint32_t *>(&xv);
+                    uint4 yv;
+                    uint32_t *yw = reinterpret_cast<uint32_t *>(&yv);
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162 *>(&xw[e2]);
+                        float x0 = __low2float(x2), x1 = __high2float(x2);
+                        if (a.sign_in) {
+                            x0 *= sg[2 * e2];
+                            x1 *= sg[2 * e2 + 1];
+                        }
+                        float y0 = x0 - __uint_as_float(r[8 * q8 + 2 * e2]);
+                        float y1 = x1 - __uint_as_float(r[8 * q8 + 2 * e2 + 1]);
+                        if (a.sign_out) {
+                            y0 *= sg[2 * e2];
+                            y1 *= sg[2 * e2 + 1];
+                        }
+                        yw[e2] = pack_bf16(y0, y1);
+                    }
+                    *g = yv;
+                }
+                tc::fence_proxy_async();           // y visible to the TMA store
+                tc::named_barrier(1, 128);         // the four epilogue warps
+                if (leader) {
+                    tc::tma_store_2d(&mapY, ering + e * kEBox, col0, row0);
+                    tc::bulk_commit_group();
+                    // the previous box's store has read shared memory: its stage is free
+                    tc::bulk_wait_read<1>();
+                    if (ei > 0) tc::mbar_arrive(&B.eempty[(ei - 1) % NE]);
+                }
             }
         }
-        tc::mma_commit(&zbar);
+        if (leader) tc::bulk_wait<0>();  // every store written before the kernel ends
     }
-    wait(&zbar, 0);
-    tc::tc_fence_after();
-
-    // ---- Z (FP32, tensor memory) -> BF16 operand in shared memory ----------------------------
-    {
-        const int m = warp * 32 + lane;
-        for (int c = 0; c < PB / 32; ++c) {
-            uint32_t r[32];
-            tc::tmem_ld32(tz + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint4 w;
-                w.x = pack_bf16(__uint_as_float(r[8 * q + 0]), __uint_as_float(r[8 * q + 1]));
-                w.y = pack_bf16(__uint_as_float(r[8 * q + 2]), __uint_as_float(r[8 * q + 3]));
-                w.z = pack_bf16(__uint_as_float(r[8 * q + 4]), __uint_as_float(r[8 * q + 5]));
-                w.w = pack_bf16(__uint_as_float(r[8 * q + 6]), __uint_as_float(r[8 * q + 7]));
-                *reinterpret_cast<uint4 *>(Zs + tc::sw128_offset(m, c * 32 + 8 * q, kTileM)) = w;
-            }
-        }
-    }
-    tc::fence_proxy_async();
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-
-    // ---- GEMM 2: acc = Z V'^T per chunk of 128 columns; y = x - acc --------------------------
-    const uint32_t id2 = tc::idesc_bf16(kTileM, kChunkN);
-    auto load2 = [&](int nc, int s) {
-        tc::mbar_expect_tx(&full[s], bytesB2);
-        for (int kb = 0; kb < PB / 64; ++kb)
-            tc::tma_load_2d(stage[s] + kb * (kChunkN * 128), &mapVp, kb * 64, vpbase + nc * kChunkN,
-                            &full[s]);
-    };
-    auto mma2 = [&](int nc) {
-        const int s = nc & 1;
-        // full[s] phases: GEMM 1 used ceil(KC/2) or floor(KC/2) of them
-        const int used = (KC + 1 - s) / 2;
-        wait(&full[s], (uint32_t)((used + (nc >> 1)) & 1));
-        tc::tc_fence_after();
-        const uint32_t sz = tc::smem_u32(Zs), sb = tc::smem_u32(stage[s]);
-        for (int k = 0; k < PB / 16; ++k) {
-            const uint32_t off = (uint32_t)(k >> 2) * (kTileM * 128) + (uint32_t)(k & 3) * 32;
-            const uint32_t offb = (uint32_t)(k >> 2) * (kChunkN * 128) + (uint32_t)(k & 3) * 32;
-            tc::mma_bf16(tacc[s], tc::sdesc_sw128(sz + off), tc::sdesc_sw128(sb + offb), id2, k != 0);
-        }
-        tc::mma_commit(&accbar[s]);
-    };
-    if (tid == 0) {
-        load2(0, 0);
-        if (NC > 1) load2(1, 1);
-        mma2(0);
-    }
-    const int m = warp * 32 + lane;
-    const int64_t row = row0 + m;
-    for (int nc = 0; nc < NC; ++nc) {
-        const int s = nc & 1;
-        wait(&accbar[s], (uint32_t)((nc >> 1) & 1));
-        tc::tc_fence_after();
-        if (tid == 0) {
-            if (nc + 1 < NC) mma2(nc + 1);  // its accumulator was drained at nc - 1
-            if (nc + 2 < NC) load2(nc + 2, s);  // chunk nc's MMAs are done: stage s is free
-        }
-        for (int c = 0; c < kChunkN / 32; ++c) {
-            uint32_t r[32];
-            tc::tmem_ld32(tacc[s] + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-            const int col0 = nc * kChunkN + c * 32;
-            if (row >= a.batch || col0 >= n) continue;
-            const __nv_bfloat16 *xr = a.Xin + row * a.ldx;
-            __nv_bfloat16 *yr = a.Y + row * a.ldy;
-            if (col0 + 32 <= n) {
-                uint4 xv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) xv[q] = *reinterpret_cast<const uint4 *>(xr + col0 + 8 * q);
-                uint4 yv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t *xw = reinterpret_cast<const uint32_t *>(&xv[q]);
-                    uint32_t *yw = reinterpret_cast<uint32_t *>(&yv[q]);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        __nv_bfloat162 x2 = *reinterpret_cast<const __nv_bfloat162 *>(&xw[e]);
-                        float x0 = __low2float(x2), x1 = __high2float(x2);
-                        const int cc = col0 + 8 * q + 2 * e;
-                        float s0 = 1.f, s1 = 1.f;
-                        if (a.sign) {
-                            s0 = a.sign[cc];
-                            s1 = a.sign[cc + 1];
-                        }
-                        if (a.sign_in) {
-                            x0 *= s0;
-                            x1 *= s1;
-                        }
-                        float y0 = x0 - __uint_as_float(r[8 * q + 2 * e]);
-                        float y1 = x1 - __uint_as_float(r[8 * q + 2 * e + 1]);
-                        if (a.sign_out) {
-                            y0 *= s0;
-                            y1 *= s1;
-                        }
-                        yw[e] = pack_bf16(y0, y1);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4 *>(yr + col0 + 8 * q) = yv[q];
-            } else {
-                for (int e = 0; e < 32 && col0 + e < n; ++e) {
-                    const int cc = col0 + e;
-                    const float sg = a.sign ? a.sign[cc] : 1.f;
-                    float x = __bfloat162float(xr[cc]);
-                    if (a.sign_in) x *= sg;
-                    float y = x - __uint_as_float(r[e]);
-                    if (a.sign_out) y *= sg;
-                    yr[cc] = __float2bfloat16(y);
-                }
-            }
-        }
-        tc::tc_fence_before();
-        __syncthreads();
-        tc::tc_fence_after();
-    }
-    if (warp == 0) tc::tmem_dealloc(tbase, 512);
+    if (warp == 1) tc::tmem_dealloc(B.tbase, 512);
 }
 
 }  // namespace wy
@@ -435,9 +498,11 @@ hh_status wy_prepare(Plan *p, const void *U, int64_t ldu, const int8_t *sign, in
     hh_status s;
     if ((s = encode_map_bf16(&w->mapV, w->Vb, n, w->hpad, w->n8 * 2, 64, w->PB))) return s;
     if (sign && (s = encode_map_bf16(&w->mapVs, w->Vs, n, w->hpad, w->n8 * 2, 64, w->PB))) return s;
-    if ((s = encode_map_bf16(&w->mapVp, w->Vp, w->PB, (uint64_t)w->P * n, w->PB * 2, 64, 128)))
+    if ((s = encode_map_bf16(&w->mapVp, w->Vp, w->PB, (uint64_t)w->P * n, w->PB * 2, 64,
+                             wy::kChunkN)))
         return s;
-    if ((s = encode_map_bf16(&w->mapVpp, w->Vpp, w->PB, (uint64_t)w->P * n, w->PB * 2, 64, 128)))
+    if ((s = encode_map_bf16(&w->mapVpp, w->Vpp, w->PB, (uint64_t)w->P * n, w->PB * 2, 64,
+                             wy::kChunkN)))
         return s;
     return HH_OK;
 }
@@ -486,23 +551,32 @@ hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void
         attr = true;
     }
     const int64_t tiles = (batch + wy::kTileM - 1) / wy::kTileM;
-    if (tiles > 0x7fffffffLL) return fail(HH_ERR_INVALID_ARG, "batch too large");
+    if (tiles * wy::kTileM > 0x7fffffffLL) return fail(HH_ERR_INVALID_ARG, "batch too large");
+    const int grid = (int)std::min<int64_t>(tiles, p->num_sms > 0 ? p->num_sms : 1);
+    // shared memory: Z operand, then as many epilogue boxes (up to 4) as leave
+    // room for at least two operand stages, then the operand ring
+    const size_t stage_bytes = 128 * 128 + (size_t)w->PB * 128;
+    const size_t avail = wy::kSmemBytes - 1024 - (size_t)w->PB * 256;
+    int estages = 4;
+    while (estages > 1 && avail < estages * (size_t)wy::kEBox + 2 * stage_bytes) --estages;
+    const int stages = (int)std::min<size_t>(wy::kMaxStages,
+                                             (avail - estages * (size_t)wy::kEBox) / stage_bytes);
+    if (stages < 2) return fail(HH_ERR_UNSUPPORTED, "compact-WY path: panel too wide for shared memory");
     for (int i = 0; i < w->P; ++i) {
         // W = W_1 ... W_P: W applies panel P first; W^T applies panel 1 first.
         const int panel = mode == HH_MODE_W ? w->P - 1 - i : i;
         const void *in = i == 0 ? X : Y;
         const int64_t ldin = i == 0 ? ldx : ldy;
-        CUtensorMap mapX;
+        CUtensorMap mapX, mapY;
         hh_status s = encode_map_bf16(&mapX, in, p->n, batch, (uint64_t)ldin * 2, 64, wy::kTileM);
+        if (!s) s = encode_map_bf16(&mapY, Y, p->n, batch, (uint64_t)ldy * 2, 64, wy::kTileM);
         if (s) return s;
         wy::PanelArgs a;
-        a.Xin = (const __nv_bfloat16 *)in;
-        a.ldx = ldin;
-        a.Y = (__nv_bfloat16 *)Y;
-        a.ldy = ldy;
-        a.batch = batch;
+        a.tiles = tiles;
+        a.estages = estages;
         a.n = (int)p->n;
         a.PB = w->PB;
+        a.stages = stages;
         a.panel = panel;
         a.sign = w->sign;
         a.sign_out = mode == HH_MODE_W && i == w->P - 1 && w->sign;
@@ -511,7 +585,7 @@ hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void
         const CUtensorMap &mv = a.sign_in ? w->mapVs : w->mapV;
         // W: Y = X - Z (V T)^T; W^T: Y = X - Z (V T^T)^T
         const CUtensorMap &mvp = mode == HH_MODE_W ? w->mapVpp : w->mapVp;
-        wy::wy_panel_kernel<<<(unsigned)tiles, wy::kThreads, wy::kSmemBytes, st>>>(mapX, mv, mvp, a);
+        wy::wy_panel_kernel<<<grid, wy::kThreads, wy::kSmemBytes, st>>>(mapX, mv, mvp, mapY, a);
         cudaError_t e = cudaGetLastError();
         if (e) return cuda_fail(e, "compact-WY launch");
     }

@@ -59,6 +59,14 @@ def test_wy_parity(mode, n, h, B):
     _wy_case(mode, n, h, B, seed=n + h)
 
 
+@pytest.mark.parametrize("mode", ["W", "WT"])
+@pytest.mark.parametrize("n,h,B", [(256, 128, 20000), (520, 192, 19500), (128, 64, 40001)])
+def test_wy_parity_many_tiles(mode, n, h, B):
+    """More 128-row tiles than SMs: each persistent CTA walks several tiles, so
+    the next tile's GEMM 1 overlaps the previous tile's epilogue."""
+    _wy_case(mode, n, h, B, seed=n + h + 1)
+
+
 def test_wy_no_sign_and_in_place():
     for mode in ("W", "WT"):
         _wy_case(mode, 1024, 128, 200, with_sign=False)
