@@ -50,7 +50,7 @@ namespace wy {
 constexpr int kTileM = 128;     // rows per tile (M of both GEMMs)
 constexpr int kChunkN = 64;     // output columns per GEMM 2 accumulator
 constexpr int kNumAcc = 4;      // accumulators, tensor-memory columns 256 + 64a
-constexpr int kThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kThreads = 224;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue, warp 6 TMA
 constexpr int kMaxStages = 8;
 constexpr uint32_t kEBox = kTileM * kChunkN * 2;  // epilogue box, 128 x 64 BF16 = 16 KB
 // Dynamic shared memory: 1 KB alignment slack, Z (PB x 256 B), the epilogue
@@ -181,7 +181,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];    // operand ring
     uint64_t efull[kMaxStages], eempty[kMaxStages];  // epilogue ring (x in, y out)
-    uint64_t z_full, z_free;                         // Z in tensor memory: written / drained
+    uint64_t z_full;                                 // Z in tensor memory written
     uint64_t zs_full, zs_free;                       // Z as BF16 operand in shared memory
     uint64_t acc_full[kNumAcc], acc_empty[kNumAcc];
     uint32_t tbase;
@@ -235,7 +235,6 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
             tc::mbar_init(&B.eempty[s], 1);
         }
         tc::mbar_init(&B.z_full, 1);
-        tc::mbar_init(&B.z_free, 4);
         tc::mbar_init(&B.zs_full, 4);
         tc::mbar_init(&B.zs_free, 1);
         for (int c = 0; c < kNumAcc; ++c) {
@@ -264,35 +263,58 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         }
     };
 
+    // Order of the operand ring and of the MMAs, per tile i (tiles of this CTA
+    // t_0, t_1, ...): GEMM 1 of t_0 alone; then for each tile, output chunk j
+    // of GEMM 2 (tile i) is followed by K chunk j of GEMM 1 of tile i+1 while
+    // both remain, then the rest of either.  The next tile's X streams in while
+    // this tile's epilogue runs, and the tensor pipe works on both.
+    const int64_t first = blockIdx.x, step = gridDim.x;
+    const int steps = NC > KC ? NC : KC;
     if (warp == 0) {
-        // ---- TMA producer -------------------------------------------------------------------
+        // ---- TMA producer: operand ring ----------------------------------------------------
         if (lane == 0) {
-            uint32_t it = 0, ei = 0;
-            for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
-                const int row0 = (int)(tile * kTileM);
-                for (int kc = 0; kc < KC; ++kc, ++it) {
-                    const uint32_t s = it % NS;
-                    wait(&B.empty[s], ((it / NS) & 1) ^ 1);
-                    unsigned char *st = ring + s * stage_bytes;
-                    tc::mbar_expect_tx(&B.full[s], bytesX + bytesV);
-                    tc::tma_load_2d(st, &mapX, kc * 64, row0, &B.full[s]);
-                    tc::tma_load_2d(st + bytesX, &mapV, kc * 64, ybase, &B.full[s]);
+            uint32_t it = 0;
+            auto load1 = [&](int64_t tile, int kc) {
+                const uint32_t s = it % NS;
+                wait(&B.empty[s], ((it / NS) & 1) ^ 1);
+                unsigned char *st = ring + s * stage_bytes;
+                tc::mbar_expect_tx(&B.full[s], bytesX + bytesV);
+                tc::tma_load_2d(st, &mapX, kc * 64, (int)(tile * kTileM), &B.full[s]);
+                tc::tma_load_2d(st + bytesX, &mapV, kc * 64, ybase, &B.full[s]);
+                ++it;
+            };
+            auto load2 = [&](int nc) {
+                const uint32_t s = it % NS;
+                wait(&B.empty[s], ((it / NS) & 1) ^ 1);
+                unsigned char *st = ring + s * stage_bytes;
+                tc::mbar_expect_tx(&B.full[s], (uint32_t)PB * 128);
+                for (int kb = 0; kb < PB / 64; ++kb)
+                    tc::tma_load_2d(st + kb * (kChunkN * 128), &mapVp, kb * 64, vpbase + nc * kChunkN,
+                                    &B.full[s]);
+                ++it;
+            };
+            if (first < a.tiles)
+                for (int kc = 0; kc < KC; ++kc) load1(first, kc);
+            for (int64_t tile = first; tile < a.tiles; tile += step) {
+                const bool next = tile + step < a.tiles;
+                for (int j = 0; j < steps; ++j) {
+                    if (j < NC) load2(NC - 1 - j);
+                    if (next && j < KC) load1(tile + step, j);
                 }
-                for (int j = 0; j < NC; ++j, ++it, ++ei) {
-                    const int nc = NC - 1 - j;
-                    const uint32_t s = it % NS;
-                    wait(&B.empty[s], ((it / NS) & 1) ^ 1);
-                    unsigned char *st = ring + s * stage_bytes;
-                    tc::mbar_expect_tx(&B.full[s], (uint32_t)PB * 128);
-                    for (int kb = 0; kb < PB / 64; ++kb)
-                        tc::tma_load_2d(st + kb * (kChunkN * 128), &mapVp, kb * 64,
-                                        vpbase + nc * kChunkN, &B.full[s]);
+            }
+        }
+    } else if (warp == 6) {
+        // ---- TMA producer: epilogue boxes of X ----------------------------------------------
+        if (lane == 0) {
+            uint32_t ei = 0;
+            for (int64_t tile = first; tile < a.tiles; tile += step)
+                for (int j = 0; j < NC; ++j, ++ei) {
                     const uint32_t e = ei % NE;
                     wait(&B.eempty[e], ((ei / NE) & 1) ^ 1);
                     tc::mbar_expect_tx(&B.efull[e], kEBox);
-                    tc::tma_load_2d(ering + e * kEBox, &mapX, nc * kChunkN, row0, &B.efull[e]);
+                    tc::tma_load_2d(ering + e * kEBox, &mapX, (NC - 1 - j) * kChunkN,
+                                    (int)(tile * kTileM), &B.efull[e]);
                 }
-            }
         }
     } else if (warp == 1) {
         // ---- MMA issuer ---------------------------------------------------------------------
@@ -301,41 +323,51 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
             const uint32_t id2 = tc::idesc_bf16(kTileM, kChunkN);
             const uint32_t sz = tc::smem_u32(Zs);
             uint32_t it = 0, ai = 0, ti = 0;
-            for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++ti) {
-                wait(&B.z_free, (ti & 1) ^ 1);  // the epilogue has moved the previous Z
+            auto mma1 = [&](int kc) {
+                const uint32_t s = it % NS;
+                wait(&B.full[s], (it / NS) & 1);
                 tc::tc_fence_after();
-                for (int kc = 0; kc < KC; ++kc, ++it) {
-                    const uint32_t s = it % NS;
-                    wait(&B.full[s], (it / NS) & 1);
-                    tc::tc_fence_after();
-                    const uint32_t sa = tc::smem_u32(ring + s * stage_bytes), sb = sa + bytesX;
+                const uint32_t sa = tc::smem_u32(ring + s * stage_bytes), sb = sa + bytesX;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        tc::mma_bf16(tz, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k),
-                                     id1, (kc | k) != 0);
-                    tc::mma_commit(&B.empty[s]);
-                }
-                tc::mma_commit(&B.z_full);
-                wait(&B.zs_full, ti & 1);  // Z as BF16 operand is in shared memory
+                for (int k = 0; k < 4; ++k)
+                    tc::mma_bf16(tz, tc::sdesc_sw128(sa + 32 * k), tc::sdesc_sw128(sb + 32 * k), id1,
+                                 (kc | k) != 0);
+                tc::mma_commit(&B.empty[s]);
+                ++it;
+            };
+            auto mma2 = [&]() {
+                const uint32_t c = ai % kNumAcc;
+                wait(&B.acc_empty[c], ((ai / kNumAcc) & 1) ^ 1);
+                const uint32_t s = it % NS;
+                wait(&B.full[s], (it / NS) & 1);
                 tc::tc_fence_after();
-                for (int j = 0; j < NC; ++j, ++it, ++ai) {
-                    const uint32_t c = ai % kNumAcc;
-                    wait(&B.acc_empty[c], ((ai / kNumAcc) & 1) ^ 1);
-                    const uint32_t s = it % NS;
-                    wait(&B.full[s], (it / NS) & 1);
-                    tc::tc_fence_after();
-                    const uint32_t sb = tc::smem_u32(ring + s * stage_bytes);
-                    const uint32_t tacc = tz + 256 + c * kChunkN;
-                    for (int k = 0; k < PB / 16; ++k) {
-                        const uint32_t offa = (uint32_t)(k >> 2) * (kTileM * 128) + (uint32_t)(k & 3) * 32;
-                        const uint32_t offb = (uint32_t)(k >> 2) * (kChunkN * 128) + (uint32_t)(k & 3) * 32;
-                        tc::mma_bf16(tacc, tc::sdesc_sw128(sz + offa), tc::sdesc_sw128(sb + offb), id2,
-                                     k != 0);
-                    }
-                    tc::mma_commit(&B.empty[s]);
-                    tc::mma_commit(&B.acc_full[c]);
+                const uint32_t sb = tc::smem_u32(ring + s * stage_bytes);
+                const uint32_t tacc = tz + 256 + c * kChunkN;
+                for (int k = 0; k < PB / 16; ++k) {
+                    const uint32_t offa = (uint32_t)(k >> 2) * (kTileM * 128) + (uint32_t)(k & 3) * 32;
+                    const uint32_t offb = (uint32_t)(k >> 2) * (kChunkN * 128) + (uint32_t)(k & 3) * 32;
+                    tc::mma_bf16(tacc, tc::sdesc_sw128(sz + offa), tc::sdesc_sw128(sb + offb), id2,
+                                 k != 0);
                 }
-                tc::mma_commit(&B.zs_free);  // GEMM 2 of this tile has read Z
+                tc::mma_commit(&B.empty[s]);
+                tc::mma_commit(&B.acc_full[c]);
+                ++it;
+                ++ai;
+            };
+            if (first < a.tiles) {
+                for (int kc = 0; kc < KC; ++kc) mma1(kc);
+                tc::mma_commit(&B.z_full);
+            }
+            for (int64_t tile = first; tile < a.tiles; tile += step, ++ti) {
+                const bool next = tile + step < a.tiles;
+                wait(&B.zs_full, ti & 1);  // Z of this tile is in shared memory; Z's columns are free
+                tc::tc_fence_after();
+                for (int j = 0; j < steps; ++j) {
+                    if (j < NC) mma2();
+                    if (next && j < KC) mma1(j);
+                }
+                if (next) tc::mma_commit(&B.z_full);
+                tc::mma_commit(&B.zs_free);  // GEMM 2 of this tile has read Zs
             }
             if (ti > 0) wait(&B.zs_free, (ti - 1) & 1);  // last commit landed before exit
         }
@@ -367,10 +399,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
             tc::fence_proxy_async();
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                tc::mbar_arrive(&B.zs_full);
-                tc::mbar_arrive(&B.z_free);
-            }
+            if (lane == 0) tc::mbar_arrive(&B.zs_full);
             for (int j = 0; j < NC; ++j, ++ai, ++ei) {
                 const int nc = NC - 1 - j;
                 const uint32_t c = ai % kNumAcc;
