@@ -49,12 +49,15 @@ namespace wy {
 
 constexpr int kTileM = 128;     // rows per tile (M of both GEMMs)
 constexpr int kChunkN = 64;     // output columns per GEMM 2 accumulator
-constexpr int kNumAcc = 4;      // accumulators, tensor-memory columns 256 + 64a
+constexpr int kNumAcc = 2;      // GEMM 2 accumulators, tensor-memory columns 384 + 64a
+// Tensor-memory columns: Z (FP32, GEMM 1's accumulator) [0, 256), Z as BF16
+// (GEMM 2's A operand, two per column) [256, 384), accumulators [384, 512).
+constexpr uint32_t kTmemZb = 256, kTmemAcc = 384;
 constexpr int kThreads = 224;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue, warp 6 TMA
 constexpr int kMaxStages = 8;
 constexpr uint32_t kEBox = kTileM * kChunkN * 2;  // epilogue box, 128 x 64 BF16 = 16 KB
-// Dynamic shared memory: 1 KB alignment slack, Z (PB x 256 B), the epilogue
-// ring and the operand ring; sized per plan by the host (panel_layout).
+// Dynamic shared memory: 1 KB alignment slack, the epilogue ring and the
+// operand ring; their stage counts are set per plan by the host.
 constexpr size_t kSmemBytes = 220 * 1024;
 
 // ---- create-time kernels (FP64) ---------------------------------------------------------
@@ -182,24 +185,25 @@ struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];    // operand ring
     uint64_t efull[kMaxStages], eempty[kMaxStages];  // epilogue ring (x in, y out)
     uint64_t z_full;                                 // Z in tensor memory written
-    uint64_t zs_full, zs_free;                       // Z as BF16 operand in shared memory
+    uint64_t zs_full, zs_free;                       // Z as BF16 operand in tensor memory
     uint64_t acc_full[kNumAcc], acc_empty[kNumAcc];
     uint32_t tbase;
     int aborted;
 };
 
 // Persistent, warp-specialised panel kernel: one CTA per SM walks 128-row
-// tiles.  Shared memory: Z as GEMM 2's BF16 operand (128 x PB), an epilogue ring
-// of 128 x 64 boxes of X (y is written over x and stored from there), and an
-// operand ring.  Warp 0 (one thread) issues every TMA load, in the order the
-// consumers need them: per tile the K chunks of GEMM 1 (an X box and a V box),
-// then per output chunk a V' box set (GEMM 2) and an X box (epilogue).  Warp 1
-// (one thread) issues the MMAs: GEMM 1 into Z (tensor-memory columns [0, PB)),
-// then GEMM 2 per 64-column chunk into one of four accumulators (columns
-// 256 + 64a).  Warps 2..5 (one tensor-memory lane quadrant each, one row per
-// thread) move Z to shared memory, then per chunk compute y = x - acc in the
-// epilogue box; one thread stores the box by TMA.  GEMM 1 of the next tile
-// starts once Z has been moved.  Chunks run from the last column to the first,
+// tiles.  Shared memory holds an epilogue ring of 128 x 64 boxes of X (y is
+// written over x and stored from there) and an operand ring.  Warp 0 (one
+// thread) issues the operand loads by TMA in the order the MMAs consume them:
+// GEMM 1 K chunks (an X box and a V box) and GEMM 2 output chunks (V' boxes).
+// Warp 6 (one thread) loads the epilogue boxes.  Warp 1 (one thread) issues the
+// MMAs: GEMM 1 into Z (FP32, tensor-memory columns [0, 256)); GEMM 2 per
+// 64-column chunk, A = Z as BF16 in tensor memory (columns [256, 384)), into
+// one of two accumulators (columns 384 + 64a).  GEMM 1 of the next tile is
+// interleaved with GEMM 2 of the current one, chunk by chunk.  Warps 2..5 (one
+// tensor-memory lane quadrant each, one row per thread) convert Z to BF16 in
+// tensor memory, then per chunk compute y = x - acc in the epilogue box; one
+// thread stores the box by TMA.  Chunks run from the last column to the first,
 // so the X boxes GEMM 1 read last are read again first (more L2 hits).  TMA
 // zero-fills loads and clips stores at the tensor's edges (rows past the
 // batch, columns past n).
@@ -211,8 +215,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
     unsigned char *smem =
         reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int n = a.n, PB = a.PB, NS = a.stages, NE = a.estages;
-    unsigned char *Zs = smem;
-    unsigned char *ering = Zs + (size_t)PB * 256;
+    unsigned char *ering = smem;
     unsigned char *ring = ering + (size_t)NE * kEBox;
     __shared__ Bars B;
 
@@ -321,7 +324,6 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         if (lane == 0) {
             const uint32_t id1 = tc::idesc_bf16(kTileM, PB);
             const uint32_t id2 = tc::idesc_bf16(kTileM, kChunkN);
-            const uint32_t sz = tc::smem_u32(Zs);
             uint32_t it = 0, ai = 0, ti = 0;
             auto mma1 = [&](int kc) {
                 const uint32_t s = it % NS;
@@ -342,12 +344,10 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                 wait(&B.full[s], (it / NS) & 1);
                 tc::tc_fence_after();
                 const uint32_t sb = tc::smem_u32(ring + s * stage_bytes);
-                const uint32_t tacc = tz + 256 + c * kChunkN;
+                const uint32_t tacc = tz + kTmemAcc + c * kChunkN;
                 for (int k = 0; k < PB / 16; ++k) {
-                    const uint32_t offa = (uint32_t)(k >> 2) * (kTileM * 128) + (uint32_t)(k & 3) * 32;
                     const uint32_t offb = (uint32_t)(k >> 2) * (kChunkN * 128) + (uint32_t)(k & 3) * 32;
-                    tc::mma_bf16(tacc, tc::sdesc_sw128(sz + offa), tc::sdesc_sw128(sb + offb), id2,
-                                 k != 0);
+                    tc::mma_bf16_ts(tacc, tz + kTmemZb + 8 * k, tc::sdesc_sw128(sb + offb), id2, k != 0);
                 }
                 tc::mma_commit(&B.empty[s]);
                 tc::mma_commit(&B.acc_full[c]);
@@ -360,14 +360,14 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
             }
             for (int64_t tile = first; tile < a.tiles; tile += step, ++ti) {
                 const bool next = tile + step < a.tiles;
-                wait(&B.zs_full, ti & 1);  // Z of this tile is in shared memory; Z's columns are free
+                wait(&B.zs_full, ti & 1);  // Z of this tile is in BF16 columns; the FP32 ones are free
                 tc::tc_fence_after();
                 for (int j = 0; j < steps; ++j) {
                     if (j < NC) mma2();
                     if (next && j < KC) mma1(j);
                 }
                 if (next) tc::mma_commit(&B.z_full);
-                tc::mma_commit(&B.zs_free);  // GEMM 2 of this tile has read Zs
+                tc::mma_commit(&B.zs_free);  // GEMM 2 of this tile has read the BF16 Z
             }
             if (ti > 0) wait(&B.zs_free, (ti - 1) & 1);  // last commit landed before exit
         }
@@ -381,22 +381,17 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         for (int64_t tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, ++ti) {
             const int row0 = (int)(tile * kTileM);
             wait(&B.z_full, ti & 1);
-            wait(&B.zs_free, (ti & 1) ^ 1);  // GEMM 2 of the previous tile has read Zs
+            wait(&B.zs_free, (ti & 1) ^ 1);  // GEMM 2 of the previous tile has read the BF16 Z
             tc::tc_fence_after();
             for (int c = 0; c < PB / 32; ++c) {
-                uint32_t r[32];
+                uint32_t r[32], w[16];
                 tc::tmem_ld32(tz + lane_off + (uint32_t)(c * 32), r);
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    uint4 w;
-                    w.x = pack_bf16(__uint_as_float(r[8 * qq + 0]), __uint_as_float(r[8 * qq + 1]));
-                    w.y = pack_bf16(__uint_as_float(r[8 * qq + 2]), __uint_as_float(r[8 * qq + 3]));
-                    w.z = pack_bf16(__uint_as_float(r[8 * qq + 4]), __uint_as_float(r[8 * qq + 5]));
-                    w.w = pack_bf16(__uint_as_float(r[8 * qq + 6]), __uint_as_float(r[8 * qq + 7]));
-                    *reinterpret_cast<uint4 *>(Zs + tc::sw128_offset(m, c * 32 + 8 * qq, kTileM)) = w;
-                }
+                for (int i = 0; i < 16; ++i)
+                    w[i] = pack_bf16(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                tc::tmem_st16(tz + lane_off + kTmemZb + (uint32_t)(c * 16), w);
             }
-            tc::fence_proxy_async();
+            tc::tmem_wait_st();
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&B.zs_full);
@@ -407,8 +402,9 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                 wait(&B.acc_full[c], (ai / kNumAcc) & 1);
                 tc::tc_fence_after();
                 uint32_t r[kChunkN];
-                tc::tmem_ld32(tz + lane_off + 256 + c * kChunkN, *reinterpret_cast<uint32_t(*)[32]>(r));
-                tc::tmem_ld32(tz + lane_off + 256 + c * kChunkN + 32,
+                tc::tmem_ld32(tz + lane_off + kTmemAcc + c * kChunkN,
+                              *reinterpret_cast<uint32_t(*)[32]>(r));
+                tc::tmem_ld32(tz + lane_off + kTmemAcc + c * kChunkN + 32,
                               *reinterpret_cast<uint32_t(*)[32]>(r + 32));
                 tc::tc_fence_before();
                 __syncwarp();
@@ -582,12 +578,12 @@ hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void
     const int64_t tiles = (batch + wy::kTileM - 1) / wy::kTileM;
     if (tiles * wy::kTileM > 0x7fffffffLL) return fail(HH_ERR_INVALID_ARG, "batch too large");
     const int grid = (int)std::min<int64_t>(tiles, p->num_sms > 0 ? p->num_sms : 1);
-    // shared memory: Z operand, then as many epilogue boxes (up to 4) as leave
-    // room for at least two operand stages, then the operand ring
+    // shared memory: as many epilogue boxes (up to 4) as leave room for at
+    // least three operand stages, then the operand ring
     const size_t stage_bytes = 128 * 128 + (size_t)w->PB * 128;
-    const size_t avail = wy::kSmemBytes - 1024 - (size_t)w->PB * 256;
+    const size_t avail = wy::kSmemBytes - 1024;
     int estages = 4;
-    while (estages > 1 && avail < estages * (size_t)wy::kEBox + 2 * stage_bytes) --estages;
+    while (estages > 1 && avail < estages * (size_t)wy::kEBox + 3 * stage_bytes) --estages;
     const int stages = (int)std::min<size_t>(wy::kMaxStages,
                                              (avail - estages * (size_t)wy::kEBox) / stage_bytes);
     if (stages < 2) return fail(HH_ERR_UNSUPPORTED, "compact-WY path: panel too wide for shared memory");
