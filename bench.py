@@ -613,9 +613,14 @@ def oracle_units(names):
             wts /= wts.sum()
 
             def f(c, Us=Us, pools=pools, wts=wts):
-                # c vectors spread over the transforms in proportion to their batches
-                for U, P, k in zip(Us, pools, np.maximum(1, np.floor(c * wts)).astype(int)):
-                    oracle.apply("W", U, np.resize(P, (k, P.shape[1])))
+                # exactly c vectors, spread over the transforms in proportion to
+                # their batches (largest remainders take the leftover vectors)
+                share = c * wts
+                k = np.floor(share).astype(int)
+                k[np.argsort(k - share)[:c - int(k.sum())]] += 1
+                for U, P, ki in zip(Us, pools, k):
+                    if ki > 0:
+                        oracle.apply("W", U, np.resize(P, (ki, P.shape[1])))
             fns[nm] = f
         elif nm == "adjoint_SYM":
             U, d = si.reflectors(N_ADJ, H_ADJ, seed=9), si.spectrum(N_ADJ, seed=9)
