@@ -216,7 +216,12 @@ __device__ __forceinline__ void chain(
             for (int q = 0; q < NV; ++q) z[q] = __shfl_sync(0xffffffffu, v, q * L);
         } else {
             if ((lane & (L - 1)) == 0) red[fused::red_index<RG, NV, NW>(buf, rg, lane / L, warp)] = v;
-            __syncthreads();
+            // only this row group's warps meet here (named barrier 1 + rg with
+            // several groups), so row groups do not wait for one another
+            if constexpr (RG > 1)
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "n"(G) : "memory");
+            else
+                __syncthreads();
             const int idx = lane / L, sub = lane & (L - 1);
             float q = 0.f;
 #pragma unroll
