@@ -28,6 +28,11 @@
 
 #include "hh_fused.cuh"
 
+// Rows per thread of the F32 adjoint for 128 < n <= 1024.
+#ifndef HH_BWD_RT
+#define HH_BWD_RT 4
+#endif
+
 namespace hh {
 namespace bwd {
 
@@ -79,6 +84,20 @@ __device__ __forceinline__ void load_cols(T (&c)[BCfg<T, G, NG, RT>::E], const T
     }
 }
 
+// c0 += a0 * b0, c1 += a1 * b1: one packed FP32 FMA for float, two FMAs for
+// double.  The per-element loops below go in pairs of columns.
+__device__ __forceinline__ void fma_pair(float &c0, float &c1, float a0, float a1, float b0,
+                                         float b1) {
+    const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(b0, b1), make_float2(c0, c1));
+    c0 = r.x;
+    c1 = r.y;
+}
+__device__ __forceinline__ void fma_pair(double &c0, double &c1, double a0, double a1, double b0,
+                                         double b1) {
+    c0 = fma(a0, b0, c0);
+    c1 = fma(a1, b1, c1);
+}
+
 // Sum NV per-thread values over the G threads of the CTA; every thread gets
 // all NV sums.  One CTA barrier (double-buffered shared partials).
 template <typename T, int G, int NG, int RT>
@@ -111,21 +130,22 @@ __device__ __forceinline__ void forward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
                                              int warp, T *red, int &buf) {
     using C = BCfg<T, G, NG, RT>;
     constexpr int E = C::E;
+    static_assert(E % 2 == 0, "columns go in pairs");
     T p[C::NV];
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
-        T s = 0;
+        T s0 = 0, s1 = 0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) s = fma(a[r][e], v[e], s);
-        p[r] = s;
+        for (int e = 0; e < E; e += 2) fma_pair(s0, s1, a[r][e], a[r][e + 1], v[e], v[e + 1]);
+        p[r] = s0 + s1;
         p[RT + r] = T(0);
     }
     cta_sum<T, G, NG, RT>(p, lane, warp, red, buf);
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
-        const T c = tk * p[r];
+        const T c = -tk * p[r];
 #pragma unroll
-        for (int e = 0; e < E; ++e) a[r][e] = fma(-c, v[e], a[r][e]);
+        for (int e = 0; e < E; e += 2) fma_pair(a[r][e], a[r][e + 1], c, c, v[e], v[e + 1]);
     }
 }
 
@@ -140,17 +160,18 @@ __device__ __forceinline__ void backward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
                                               int warp, T *red, int &buf) {
     using C = BCfg<T, G, NG, RT>;
     constexpr int E = C::E, VEC = C::VEC;
+    static_assert(E % 2 == 0, "columns go in pairs");
     T p[C::NV];
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
-        T sa = 0, sg = 0;
+        T sa0 = 0, sa1 = 0, sg0 = 0, sg1 = 0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            sa = fma(a[r][e], v[e], sa);
-            sg = fma(g[r][e], v[e], sg);
+        for (int e = 0; e < E; e += 2) {
+            fma_pair(sa0, sa1, a[r][e], a[r][e + 1], v[e], v[e + 1]);
+            fma_pair(sg0, sg1, g[r][e], g[r][e + 1], v[e], v[e + 1]);
         }
-        p[r] = sa;
-        p[RT + r] = sg;
+        p[r] = sa0 + sa1;
+        p[RT + r] = sg0 + sg1;
     }
     cta_sum<T, G, NG, RT>(p, lane, warp, red, buf);
     T acc[E];
@@ -160,13 +181,14 @@ __device__ __forceinline__ void backward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
         const T alpha = p[r], beta = p[RT + r];
-        const T ca = tk * alpha, cb = tk * beta;
+        const T ca = -tk * alpha, cb = -tk * beta, nb = -beta;
         ab += (double)alpha * (double)beta;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            a[r][e] = fma(-ca, v[e], a[r][e]);                        // a_in
-            acc[e] = fma(alpha, g[r][e], fma(-beta, a[r][e], acc[e]));  // alpha G - beta a_in
-            g[r][e] = fma(-cb, v[e], g[r][e]);                        // H G
+        for (int e = 0; e < E; e += 2) {
+            fma_pair(a[r][e], a[r][e + 1], ca, ca, v[e], v[e + 1]);                // a_in
+            fma_pair(acc[e], acc[e + 1], nb, nb, a[r][e], a[r][e + 1]);            // - beta a_in
+            fma_pair(acc[e], acc[e + 1], alpha, alpha, g[r][e], g[r][e + 1]);      // + alpha G
+            fma_pair(g[r][e], g[r][e + 1], cb, cb, v[e], v[e + 1]);                // H G
         }
     }
     if (threadIdx.x == 0) *sk += ab;
@@ -528,9 +550,9 @@ hh_status dispatch(const Plan *p, int mode, const void *S, int64_t lds, const vo
                              (T *)gU, (T *)gd, batch, vec_ok, scratch, scratch_bytes, pa, st)
     if (sizeof(T) == 4) {
         if (n <= 128) HH_RUN(32, 1, 4);
-        if (n <= 256) HH_RUN(32, 2, 2);
-        if (n <= 512) HH_RUN(64, 2, 2);
-        if (n <= 1024) HH_RUN(128, 2, 2);
+        if (n <= 256) HH_RUN(32, 2, HH_BWD_RT);
+        if (n <= 512) HH_RUN(64, 2, HH_BWD_RT);
+        if (n <= 1024) HH_RUN(128, 2, HH_BWD_RT);
         if (n <= 2048) HH_RUN(256, 2, 2);
         if (n <= 4096) HH_RUN(512, 2, 2);
     } else {
