@@ -145,7 +145,23 @@ def rel_l2(a, b):
 
 
 # --------------------------------------------------------------------------------------
-# rows: resident inputs, one call per step
+# rows: resident inputs, one call per step.  Each row's e2e() gives the bytes it moves per
+# step and its end-to-end work as chunks (copy in, compute, copy out), which
+# measure_e2e() pipelines over three streams.
+
+def pinned_copy(torch, t):
+    """A pinned host copy of device tensor t."""
+    h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+    h.copy_(t)
+    return h
+
+
+def row_chunks(B, parts):
+    """Split [0, B) into `parts` contiguous row ranges."""
+    step = -(-B // parts)
+    return [(r, min(B, r + step)) for r in range(0, B, step)]
+
+
 
 _SHARED = {}
 
@@ -197,17 +213,17 @@ class ChainRow:
 
     def e2e(self, torch):
         key = ("host", self.n, self.B)
-        if key not in _SHARED:
-            Xh = self.X.cpu().pin_memory()
-            _SHARED[key] = (Xh, torch.empty_like(Xh).pin_memory(), torch.empty_like(self.X),
-                            torch.empty_like(self.X))
-        Xh, Yh, Xd, Yd = _SHARED[key]
-
-        def step():
-            Xd.copy_(Xh, non_blocking=True)
-            self.plan.apply_mode(self.mode, Xd, out=Yd)
-            Yh.copy_(Yd, non_blocking=True)
-        return Xh.numel() * 4, Yh.numel() * 4, step
+        if key not in _SHARED:  # the three chain rows read the same host vectors
+            _SHARED[key] = pinned_copy(torch, self.X)
+        Xh = _SHARED[key]
+        Yh = torch.empty(Xh.shape, dtype=Xh.dtype, pin_memory=True)
+        Xd, Yd = torch.empty_like(self.X), torch.empty_like(self.X)
+        chunks = []
+        for r0, r1 in row_chunks(self.B, 8):
+            chunks.append((lambda a=r0, b=r1: Xd[a:b].copy_(Xh[a:b], non_blocking=True),
+                           lambda a=r0, b=r1: self.plan.apply_mode(self.mode, Xd[a:b], out=Yd[a:b]),
+                           lambda a=r0, b=r1: Yh[a:b].copy_(Yd[a:b], non_blocking=True)))
+        return Xh.numel() * 4, Yh.numel() * 4, chunks
 
 
 class WYRow:
@@ -249,15 +265,15 @@ class WYRow:
         return rel_l2(self.Y[idx].double().cpu().numpy(), ref)
 
     def e2e(self, torch):
-        Xh = self.X.cpu().pin_memory()
-        Yh = torch.empty_like(Xh).pin_memory()
+        Xh = pinned_copy(torch, self.X)
+        Yh = torch.empty(Xh.shape, dtype=Xh.dtype, pin_memory=True)
         Xd, Yd = torch.empty_like(self.X), torch.empty_like(self.X)
-
-        def step():
-            Xd.copy_(Xh, non_blocking=True)
-            self.plan.apply(Xd, out=Yd)
-            Yh.copy_(Yd, non_blocking=True)
-        return Xh.numel() * 2, Yh.numel() * 2, step
+        chunks = []
+        for r0, r1 in row_chunks(self.B, 8):
+            chunks.append((lambda a=r0, b=r1: Xd[a:b].copy_(Xh[a:b], non_blocking=True),
+                           lambda a=r0, b=r1: self.plan.apply(Xd[a:b], out=Yd[a:b]),
+                           lambda a=r0, b=r1: Yh[a:b].copy_(Yd[a:b], non_blocking=True)))
+        return Xh.numel() * 2, Yh.numel() * 2, chunks
 
 
 class MahalanobisRow:
@@ -322,25 +338,33 @@ class MahalanobisRow:
                    rel_l2(gd.double().cpu().numpy(), (z * z).sum(0)))
 
     def e2e(self, torch):
-        Xh = self.X.cpu().pin_memory()
-        iah, ibh = self.ia.cpu().pin_memory(), self.ib.cpu().pin_memory()
-        oh = torch.empty(self.P).pin_memory()
-        gUh = torch.empty(self.h, self.n).pin_memory()
+        Xh = pinned_copy(torch, self.X)
+        iah, ibh = pinned_copy(torch, self.ia), pinned_copy(torch, self.ib)
+        oh = torch.empty(self.P, pin_memory=True)
+        gUh = torch.empty(self.h, self.n, pin_memory=True)
         Xd, iad, ibd = torch.empty_like(self.X), torch.empty_like(self.ia), torch.empty_like(self.ib)
+        res = {}
 
-        def step():
+        def h2d():
             Xd.copy_(Xh, non_blocking=True)
             iad.copy_(iah, non_blocking=True)
             ibd.copy_(ibh, non_blocking=True)
+
+        def comp():
             if self.grad:
-                gU, _ = self.plan.mahalanobis_backward(Xd, iad, ibd, self.gout)
-                gUh.copy_(gU, non_blocking=True)
+                res["gU"], _ = self.plan.mahalanobis_backward(Xd, iad, ibd, self.gout)
             else:
                 self.plan.mahalanobis(Xd, iad, ibd, out=self.out)
+
+        def d2h():
+            if self.grad:
+                res["gU"].record_stream(torch.cuda.current_stream())
+                gUh.copy_(res["gU"], non_blocking=True)
+            else:
                 oh.copy_(self.out, non_blocking=True)
-        h2d = Xh.numel() * 4 + 2 * iah.numel() * 8
-        d2h = gUh.numel() * 4 if self.grad else oh.numel() * 4
-        return h2d, d2h, step
+        h2d_bytes = Xh.numel() * 4 + 2 * iah.numel() * 8
+        d2h_bytes = gUh.numel() * 4 if self.grad else oh.numel() * 4
+        return h2d_bytes, d2h_bytes, [(h2d, comp, d2h)]
 
 
 class AdjointRow:
@@ -391,17 +415,23 @@ class AdjointRow:
                    rel_l2(gd.double().cpu().numpy(), rd))
 
     def e2e(self, torch):
-        Xh, Gh = self.X.cpu().pin_memory(), self.G.cpu().pin_memory()
-        gUh = torch.empty(self.h, self.n).pin_memory()
-        Xd, Gd = torch.empty_like(self.X), torch.empty_like(self.G)
+        Xh, Gh = pinned_copy(torch, self.X), pinned_copy(torch, self.G)
+        gUh = torch.empty(self.h, self.n, pin_memory=True)
+        Xd, Gd, Yd = torch.empty_like(self.X), torch.empty_like(self.G), torch.empty_like(self.X)
+        res = {}
 
-        def step():
+        def h2d():
             Xd.copy_(Xh, non_blocking=True)
             Gd.copy_(Gh, non_blocking=True)
-            self.plan.apply_sym(Xd, out=self.Y)
-            _, gU, _ = self.plan.backward("SYM", Xd, Gd, need_gX=False)
-            gUh.copy_(gU, non_blocking=True)
-        return (Xh.numel() + Gh.numel()) * 4, gUh.numel() * 4, step
+
+        def comp():
+            self.plan.apply_sym(Xd, out=Yd)
+            _, res["gU"], _ = self.plan.backward("SYM", Xd, Gd, need_gX=False)
+
+        def d2h():
+            res["gU"].record_stream(torch.cuda.current_stream())
+            gUh.copy_(res["gU"], non_blocking=True)
+        return (Xh.numel() + Gh.numel()) * 4, gUh.numel() * 4, [(h2d, comp, d2h)]
 
 
 def c5_specs():
@@ -511,21 +541,27 @@ class BatchedRow:
                 "max_rel_diff_vs_batched": same}
 
     def e2e(self, torch):
-        Xh = torch.empty(self.Xbuf.shape, dtype=self.Xbuf.dtype, pin_memory=True)
-        Xh.copy_(self.Xbuf)
+        import paper_1811_07624_gb300 as hh
+
+        Xh = pinned_copy(torch, self.Xbuf)
         Yh = torch.empty(self.Ybuf.shape, dtype=self.Ybuf.dtype, pin_memory=True)
         Xd, Yd = torch.empty_like(self.Xbuf), torch.empty_like(self.Ybuf)
-        Xs, Ys, off = [], [], 0
-        for n, _, b, _ in self.specs:
-            Xs.append(Xd[off:off + n * b].view(b, n))
-            Ys.append(Yd[off:off + n * b].view(b, n))
-            off += n * b
-
-        def step():
-            Xd.copy_(Xh, non_blocking=True)
-            self.batch.apply(Xs, Ys, mode="W")
-            Yh.copy_(Yd, non_blocking=True)
-        return Xh.numel() * 4, Yh.numel() * 4, step
+        chunks, off, groups = [], 0, 8
+        per = -(-len(self.specs) // groups)
+        for g0 in range(0, len(self.specs), per):
+            specs = self.specs[g0:g0 + per]
+            batch = hh.Batch(self.plans[g0:g0 + per], [b for _, _, b, _ in specs])
+            Xs, Ys, o = [], [], off
+            for n, _, b, _ in specs:
+                Xs.append(Xd[o:o + n * b].view(b, n))
+                Ys.append(Yd[o:o + n * b].view(b, n))
+                o += n * b
+            chunks.append((lambda a=off, z=o: Xd[a:z].copy_(Xh[a:z], non_blocking=True),
+                           lambda bt=batch, xs=Xs, ys=Ys: bt.apply(xs, ys, mode="W"),
+                           lambda a=off, z=o: Yh[a:z].copy_(Yd[a:z], non_blocking=True)))
+            self._e2e_batches = getattr(self, "_e2e_batches", []) + [batch]
+            off = o
+        return Xh.numel() * 4, Yh.numel() * 4, chunks
 
 
 def make_rows(torch, dev, names):
@@ -639,10 +675,16 @@ def oracle_rates(names, budget_s):
     fns = oracle_units(names)
     out = {}
     for nm, f in fns.items():
-        t0 = time.perf_counter()
-        f(4)
-        dt = max(time.perf_counter() - t0, 1e-4)
-        count = int(max(4, min(1 << 18, 4 * budget_s / dt)))
+        f(4)  # first call: thread start-up, not timed
+        c = 4
+        while True:  # grow the sample until it takes a measurable time
+            t0 = time.perf_counter()
+            f(c)
+            dt = time.perf_counter() - t0
+            if dt >= 0.05 * budget_s or c >= (1 << 18):
+                break
+            c *= 4
+        count = int(max(4, min(1 << 20, c * budget_s / max(dt, 1e-6))))
         t0 = time.perf_counter()
         f(count)
         out[nm] = (count, time.perf_counter() - t0)
@@ -890,14 +932,41 @@ def compare_fp32(torch, dev, wy_rows, out_rows):
 
 
 def measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step, steps=3):
-    """The step through the public API from pinned host memory, results read back."""
+    """The step through the public API from pinned host memory, results read back.
+
+    Every row's work is split into chunks (copy in, compute, copy out); the
+    chunks of all rows are pipelined over three streams, so the copies of one
+    chunk overlap the compute of another.  Per chunk, the copy in waits for the
+    previous step's compute on that chunk, and the compute for the previous
+    step's copy out."""
     parts = [r.e2e(torch) for r in rows]
     h2d = sum(p[0] for p in parts)
     d2h = sum(p[1] for p in parts)
+    chunks = [c for p in parts for c in p[2]]
+    s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    last_comp = [None] * len(chunks)
+    last_out = [None] * len(chunks)
 
     def step():
-        for p in parts:
-            p[2]()
+        for i, (cin, comp, cout) in enumerate(chunks):
+            with torch.cuda.stream(s_in):
+                if last_comp[i] is not None:
+                    s_in.wait_event(last_comp[i])
+                cin()
+                e_in = torch.cuda.Event()
+                e_in.record(s_in)
+            with torch.cuda.stream(s_comp):
+                s_comp.wait_event(e_in)
+                if last_out[i] is not None:
+                    s_comp.wait_event(last_out[i])
+                comp()
+                last_comp[i] = torch.cuda.Event()
+                last_comp[i].record(s_comp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(last_comp[i])
+                cout()
+                last_out[i] = torch.cuda.Event()
+                last_out[i].record(s_out)
 
     step()
     torch.cuda.synchronize()
@@ -906,8 +975,13 @@ def measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step, steps=3):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    s_in.wait_event(a)
     for _ in range(steps):
         step()
+    for s in (s_in, s_comp, s_out):
+        e = torch.cuda.Event()
+        e.record(s)
+        stream.wait_event(e)
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
@@ -916,8 +990,8 @@ def measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step, steps=3):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
     return {"value": world * vec_per_step / (ms / 1e3), "unit": "vectors/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
-
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "pipelining": f"{len(chunks)} chunks over copy-in, compute and copy-out streams"}
 
 if __name__ == "__main__":
     sys.exit(main())
