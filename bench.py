@@ -50,6 +50,7 @@ N_MAHAL, H_MAHAL, P_MAHAL, PTS_MAHAL = 256, 16, 1 << 20, 100_000
 N_ADJ, H_ADJ, B_ADJ = 1024, 32, 65_536
 C5_COUNT, C5_SCALE = 512, 1.0
 C5_TUNE_H, C5_TUNE_ROWS = [4, 8, 16, 32, 64], 32_768
+TUNE_TABLE = None  # --tune-table: load the batched launch's shapes from here, or tune and save
 ALL_ROWS = ["chain_W", "chain_WT", "chain_SYM", "wy_h64", "wy_h256", "wy_h1024", "mahalanobis",
             "mahalanobis_grad", "adjoint_SYM", "batched_C5"]
 
@@ -57,6 +58,10 @@ KERNEL_SOURCES = ["paper_1811_07624_gb300/csrc/hh_staged.cuh",
                   "paper_1811_07624_gb300/csrc/hh_fused_f32.cu",
                   "paper_1811_07624_gb300/csrc/hh_fused.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "staged_chain_n4096_h16_ncu_full.md")
+BATCHED_SOURCES = ["paper_1811_07624_gb300/csrc/hh_batched.cu",
+                   "paper_1811_07624_gb300/csrc/hh_staged.cuh",
+                   "paper_1811_07624_gb300/csrc/hh_fused.cuh"]
+BATCHED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "batched_c5_ncu_full.md")
 
 
 def dist_env():
@@ -73,17 +78,19 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "of fallback"
 
 
-def profiled_traffic(mode, batch):
-    """DRAM bytes of one chain launch from the committed ncu summary, scaled by
-    the vector count; None when the kernel sources changed since the capture."""
+def profiled_traffic(mode, batch, sources=None, path=None):
+    """DRAM bytes of one launch from a committed ncu summary, scaled by the
+    vector count; None when the kernel sources changed since the capture."""
+    sources = sources or KERNEL_SOURCES
+    path = path or TRAFFIC_FILE
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     sha = h.hexdigest()[:16]
-    if not os.path.exists(TRAFFIC_FILE):
+    if not os.path.exists(path):
         return None
-    for line in open(TRAFFIC_FILE):
+    for line in open(path):
         if line.startswith("TRAFFIC ") and f"mode={mode} " in line:
             kv = dict(t.split("=", 1) for t in line.split()[1:])
             if kv.get("sources_sha256") == sha:
@@ -454,7 +461,14 @@ class BatchedRow:
         ns = sorted({n for n, _, _, _ in self.specs})
         t0 = time.perf_counter()
         hh.tune_clear()
-        hh.tune(ns, C5_TUNE_H, rows=C5_TUNE_ROWS)
+        if TUNE_TABLE and os.path.exists(TUNE_TABLE):
+            hh.tune_load(TUNE_TABLE)  # shapes of an earlier tuning run on this GPU
+            self.tune_source = f"loaded from {TUNE_TABLE}"
+        else:
+            hh.tune(ns, C5_TUNE_H, rows=C5_TUNE_ROWS)
+            self.tune_source = f"tuned here: n in {ns[0]}..{ns[-1]}, h in {C5_TUNE_H}"
+            if TUNE_TABLE:
+                hh.tune_save(TUNE_TABLE)
         self.tune_s = time.perf_counter() - t0
         self.U = [si.reflectors(n, h, seed=sd) for n, h, _, sd in self.specs]
         self.plans = [hh.Plan(torch.tensor(U, device=dev, dtype=torch.float32)) for U in self.U]
@@ -474,6 +488,7 @@ class BatchedRow:
         info = self.batch.info()
         shapes = hh.batch_shapes()
         self.info = {"items": info["items"], "grid": info["grid"], "tune_s": self.tune_s,
+                     "tune": self.tune_source,
                      "shape_use": {f"G{shapes[k]['G']}xNG{shapes[k]['NG']}xRT{shapes[k]['RT']}":
                                    info["shapes"].count(k) for k in sorted(set(info["shapes"]))}}
 
@@ -751,9 +766,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--tune-table", default=None,
+                    help="batched launch: load tile shapes from this file if it exists, "
+                         "else tune and save them there")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     names = [r for r in args.rows.split(",") if r]
+    global TUNE_TABLE
+    TUNE_TABLE = args.tune_table
     if args.batch_scale != 1.0:
         scale_batches(args.batch_scale)
     if args.impl == "reference":
@@ -837,7 +857,11 @@ def main():
         s = ms / 1e3
         gbs, tfl = r.bytes() / s / 1e9, r.flops() / s / 1e12
         ach = gbs if r.bound == "hbm" else tfl
-        traffic = (profiled_traffic(r.mode, r.vectors()) if isinstance(r, ChainRow) else None)
+        traffic = None
+        if isinstance(r, ChainRow):
+            traffic = profiled_traffic(r.mode, r.vectors())
+        elif isinstance(r, BatchedRow):
+            traffic = profiled_traffic("C5", r.vectors(), BATCHED_SOURCES, BATCHED_TRAFFIC_FILE)
         out_rows[r.name] = {"ms": ms, "vectors_per_s": r.vectors() / s, "GB_s": gbs,
                             "TFLOP_s": tfl, "bound": r.bound, "frac": ach / peak_of[r.bound],
                             "hbm_frac": gbs / peaks["hbm_gbs"], "launches": r.launches,
