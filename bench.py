@@ -840,9 +840,9 @@ def main():
     clocks = sampler.stop()
     ms_step = t0.elapsed_time(t1) / args.steps
     if pg:
-        t = torch.tensor([ms_step], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_step = float(t.item())
+        from paper_1811_07624_gb300.sharding import reduce_max
+
+        ms_step = reduce_max(ms_step, pg, dev)  # the slowest rank's step
     vec_per_step = sum(r.vectors() for r in rows)
     value = world * vec_per_step / (ms_step / 1e3)
 
@@ -1010,9 +1010,9 @@ def measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step, steps=3):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_1811_07624_gb300.sharding import reduce_max
+
+        ms = reduce_max(ms, pg, dev)
     return {"value": world * vec_per_step / (ms / 1e3), "unit": "vectors/s", "ms_per_step": ms,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps,
             "pipelining": f"{len(chunks)} chunks over copy-in, compute and copy-out streams"}
