@@ -1,0 +1,168 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration bench.py times.
+
+Each case runs the CUDA path on the whole batch, then compares sampled outputs
+with the FP64 oracle computed for those rows alone (rows are independent), and
+checks properties that hold at any size on every output:
+  * FP32 chain (n = 1024 at 1,048,576 vectors with h = 10 and 32; n = 4096 at
+    262,144 vectors with h = 12, 16 and 64; modes W, W^T, S): sampled rows within
+    1e-5 relative L2, every row finite, |W x| = |x| per row for W and W^T;
+  * BF16 compact-WY (n = 4096, 262,144 vectors, h = 64 / 256 / 1024): sampled
+    rows within 1e-2 of the oracle on the BF16-rounded data, norms kept to 1e-2;
+  * adjoint of S (n = 1024, h = 32, 65,536 vectors): sampled rows of dL/dX
+    against the oracle; dL/dv and dL/dd add up over two halves of the batch;
+  * fast Mahalanobis distance (n = 256, h = 16, 1,048,576 pairs): sampled pairs;
+  * batched launch, 512 ragged transforms: every transform on 64 vectors.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import synthetic_inputs as si  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _sample(batch, k=192):
+    """Row indices spread over the batch, with the first and last rows."""
+    idx = np.unique(np.concatenate([np.linspace(0, batch - 1, k).astype(np.int64),
+                                    [0, 1, batch - 2, batch - 1]]))
+    return torch.as_tensor(idx, device=DEV)
+
+
+def _gaussian(batch, n, seed, dtype=torch.float32):
+    g = torch.Generator(device=DEV).manual_seed(seed)
+    return torch.randn(batch, n, device=DEV, generator=g).to(dtype)
+
+
+@pytest.mark.parametrize("n,h,batch", [(1024, 10, 1 << 20), (1024, 32, 1 << 20), (4096, 12, 262144),
+                                       (4096, 16, 262144), (4096, 64, 262144)])
+def test_fp32_chain_full_size(n, h, batch):
+    from paper_1811_07624_gb300 import Plan
+
+    U = si.reflectors(n, h, seed=n + h)
+    d = si.spectrum(n, seed=n + h)
+    s = si.sign(n, seed=n + h)
+    U32 = torch.tensor(U, dtype=torch.float32)
+    d32 = torch.tensor(d, dtype=torch.float32)
+    plan = Plan(U32.to(DEV), d=d32.to(DEV), sign=torch.tensor(s, device=DEV))
+    X = _gaussian(batch, n, seed=h)
+    Y = torch.empty_like(X)
+    idx = _sample(batch)
+    Xs = X[idx].double().cpu().numpy()
+    for mode in ("W", "WT", "SYM"):
+        Y.fill_(float("nan"))
+        plan.apply_mode(mode, X, out=Y)
+        plan.sync()
+        assert bool(torch.isfinite(Y).all()), f"{mode}: non-finite or unwritten output"
+        ref = oracle.apply(mode, U32.double().numpy(), Xs, sign=s, d=d32.double().numpy())
+        err = _rel(Y[idx].double().cpu().numpy(), ref)
+        assert err <= 1e-5, f"{mode} n={n} h={h}: {err:.2e}"
+        if mode != "SYM":
+            ratio = Y.norm(dim=1) / X.norm(dim=1)
+            assert float((ratio - 1).abs().max()) <= 1e-5, f"{mode}: norm not kept"
+    plan.close()
+
+
+@pytest.mark.parametrize("h", [64, 256, 1024])
+def test_bf16_wy_full_size(h):
+    from paper_1811_07624_gb300 import Plan
+
+    n, batch = 4096, 262144
+    Ub = torch.tensor(si.reflectors(n, h, seed=h), dtype=torch.float32).bfloat16()
+    plan = Plan(Ub.to(DEV))
+    X = _gaussian(batch, n, seed=h + 1, dtype=torch.bfloat16)
+    idx = _sample(batch, 48)
+    Xs = X[idx].double().cpu().numpy()
+    for mode in ("W", "WT"):
+        Y = plan.apply_mode(mode, X)
+        plan.sync()
+        assert bool(torch.isfinite(Y).all())
+        ref = oracle.apply(mode, Ub.double().numpy(), Xs)
+        err = _rel(Y[idx].double().cpu().numpy(), ref)
+        assert err <= 1e-2, f"{mode} h={h}: {err:.2e}"
+        ratio = Y.float().norm(dim=1) / X.float().norm(dim=1)
+        assert float((ratio - 1).abs().max()) <= 1e-2
+        del Y
+    plan.close()
+
+
+def test_adjoint_sym_full_size():
+    from paper_1811_07624_gb300 import Plan
+
+    n, h, batch = 1024, 32, 65536
+    U32 = torch.tensor(si.reflectors(n, h, seed=9), dtype=torch.float32)
+    d32 = torch.tensor(si.spectrum(n, seed=9), dtype=torch.float32)
+    plan = Plan(U32.to(DEV), d=d32.to(DEV))
+    X = _gaussian(batch, n, seed=10)
+    G = _gaussian(batch, n, seed=11)
+    gX, gU, gd = plan.backward("SYM", X, G)
+    half = batch // 2
+    _, gU1, gd1 = plan.backward("SYM", X[:half].contiguous(), G[:half].contiguous(), need_gX=False)
+    _, gU2, gd2 = plan.backward("SYM", X[half:].contiguous(), G[half:].contiguous(), need_gX=False)
+    plan.sync()
+    assert _rel((gU1 + gU2).double().cpu().numpy(), gU.double().cpu().numpy()) <= 1e-5
+    assert _rel((gd1 + gd2).double().cpu().numpy(), gd.double().cpu().numpy()) <= 1e-5
+    idx = _sample(batch, 32)
+    rX, _, _ = oracle.backward("SYM", U32.double().numpy(), X[idx].double().cpu().numpy(),
+                               G[idx].double().cpu().numpy(), d=d32.double().numpy())
+    assert _rel(gX[idx].double().cpu().numpy(), rX) <= 1e-4
+    plan.close()
+
+
+def test_mahalanobis_full_size():
+    from paper_1811_07624_gb300 import Plan
+
+    n, h, npairs = 256, 16, 1 << 20
+    Xp, labels = si.gaussian_mixture(100_000, n=n, seed=0)
+    ia, ib, _ = si.labelled_pairs(labels, npairs, seed=0)
+    U32 = torch.tensor(si.reflectors(n, h, seed=7), dtype=torch.float32)
+    d32 = torch.tensor(si.spectrum(n, seed=7), dtype=torch.float32)
+    plan = Plan(U32.to(DEV), d=d32.to(DEV))
+    Xg = torch.tensor(Xp, dtype=torch.float32, device=DEV)
+    out = plan.mahalanobis(Xg, torch.tensor(ia, device=DEV), torch.tensor(ib, device=DEV))
+    plan.sync()
+    assert bool(torch.isfinite(out).all()) and bool((out >= 0).all())
+    sel = _sample(npairs, 256).cpu().numpy()
+    ref = oracle.mahalanobis(U32.double().numpy(), Xg.double().cpu().numpy(), ia[sel], ib[sel],
+                             d32.double().numpy())
+    assert _rel(out[torch.as_tensor(sel, device=DEV)].double().cpu().numpy(), ref) <= 1e-5
+    plan.close()
+
+
+def test_batched_512_transforms_full_size():
+    import paper_1811_07624_gb300 as hh
+
+    specs = [(t["n"], t["h"], t["batch"], t["seed"]) for t in si.ragged_transforms(512)]
+    hh.tune_clear()  # the fixed shape rule; the tuned shapes are covered by the batched tests
+    Us = [torch.tensor(si.reflectors(n, h, seed=sd), dtype=torch.float32) for n, h, _, sd in specs]
+    plans = [hh.Plan(U.to(DEV)) for U in Us]
+    total = sum(n * b for n, _, b, _ in specs)
+    g = torch.Generator(device=DEV).manual_seed(77)
+    Xbuf = torch.randn(total, device=DEV, generator=g)
+    Ybuf = torch.full_like(Xbuf, float("nan"))
+    Xs, Ys, off = [], [], 0
+    for n, _, b, _ in specs:
+        Xs.append(Xbuf[off:off + n * b].view(b, n))
+        Ys.append(Ybuf[off:off + n * b].view(b, n))
+        off += n * b
+    with hh.Batch(plans, [b for _, _, b, _ in specs]) as batch:
+        batch.apply(Xs, Ys, mode="W")
+        batch.sync()
+    assert bool(torch.isfinite(Ybuf).all()), "an output was not written"
+    worst = 0.0
+    for U, X, Y in zip(Us, Xs, Ys):
+        idx = _sample(X.shape[0], 62)
+        ref = oracle.apply("W", U.double().numpy(), X[idx].double().cpu().numpy())
+        worst = max(worst, _rel(Y[idx].double().cpu().numpy(), ref))
+    assert worst <= 1e-5, f"worst transform: {worst:.2e}"
+    for p in plans:
+        p.close()
