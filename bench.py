@@ -50,6 +50,7 @@ N_MAHAL, H_MAHAL, P_MAHAL, PTS_MAHAL = 256, 16, 1 << 20, 100_000
 N_ADJ, H_ADJ, B_ADJ = 1024, 32, 65_536
 C5_COUNT, C5_SCALE = 512, 1.0
 C5_TUNE_H, C5_TUNE_ROWS = [4, 8, 16, 32, 64], 32_768
+E2E_CHUNKS = 16    # chunks per large row in the pipelined end-to-end step
 TUNE_TABLE = None  # --tune-table: load the batched launch's shapes from here, or tune and save
 ALL_ROWS = ["chain_W", "chain_WT", "chain_SYM", "wy_h64", "wy_h256", "wy_h1024", "mahalanobis",
             "mahalanobis_grad", "adjoint_SYM", "batched_C5"]
@@ -226,7 +227,7 @@ class ChainRow:
         Yh = torch.empty(Xh.shape, dtype=Xh.dtype, pin_memory=True)
         Xd, Yd = torch.empty_like(self.X), torch.empty_like(self.X)
         chunks = []
-        for r0, r1 in row_chunks(self.B, 8):
+        for r0, r1 in row_chunks(self.B, E2E_CHUNKS):
             chunks.append((lambda a=r0, b=r1: Xd[a:b].copy_(Xh[a:b], non_blocking=True),
                            lambda a=r0, b=r1: self.plan.apply_mode(self.mode, Xd[a:b], out=Yd[a:b]),
                            lambda a=r0, b=r1: Yh[a:b].copy_(Yd[a:b], non_blocking=True)))
@@ -276,7 +277,7 @@ class WYRow:
         Yh = torch.empty(Xh.shape, dtype=Xh.dtype, pin_memory=True)
         Xd, Yd = torch.empty_like(self.X), torch.empty_like(self.X)
         chunks = []
-        for r0, r1 in row_chunks(self.B, 8):
+        for r0, r1 in row_chunks(self.B, E2E_CHUNKS):
             chunks.append((lambda a=r0, b=r1: Xd[a:b].copy_(Xh[a:b], non_blocking=True),
                            lambda a=r0, b=r1: self.plan.apply(Xd[a:b], out=Yd[a:b]),
                            lambda a=r0, b=r1: Yh[a:b].copy_(Yd[a:b], non_blocking=True)))
@@ -561,7 +562,7 @@ class BatchedRow:
         Xh = pinned_copy(torch, self.Xbuf)
         Yh = torch.empty(self.Ybuf.shape, dtype=self.Ybuf.dtype, pin_memory=True)
         Xd, Yd = torch.empty_like(self.Xbuf), torch.empty_like(self.Ybuf)
-        chunks, off, groups = [], 0, 8
+        chunks, off, groups = [], 0, E2E_CHUNKS
         per = -(-len(self.specs) // groups)
         for g0 in range(0, len(self.specs), per):
             specs = self.specs[g0:g0 + per]
