@@ -14,8 +14,6 @@ constexpr int kPrepThreads = 256;
 
 template <typename T>
 __device__ inline double to_f64(T v) { return (double)v; }
-template <>
-__device__ inline double to_f64<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
 // One CTA per reflector: FP64 sum of squares (fixed-order tree), tau, |v|,
 // then the zero-padded copy in the compute type.
