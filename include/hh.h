@@ -265,6 +265,23 @@ hh_status hh_tune_save(const char *path);
 hh_status hh_tune_load(const char *path);
 hh_status hh_tune_clear(void);
 
+/*
+ * Test hooks for failure handling; the paper has no counterpart.
+ *
+ * hh_debug_fail_alloc(k): the k-th device allocation the library makes from
+ * now on (plans, batches, backward scratch) fails as if the device were out of
+ * memory, so that call returns HH_ERR_OOM having freed what it held; k = 0
+ * switches the hook off.  Host only; process-wide.
+ *
+ * hh_debug_wait_timeout(cycles, stream): runs the bounded mbarrier wait that
+ * every pipelined kernel uses on a barrier nothing arrives on, with a limit
+ * of `cycles` clock cycles (1 .. 4e9), and synchronises `stream`.  Returns
+ * HH_ERR_TIMEOUT, the expected outcome: the wait gave up and the kernel ended
+ * normally, leaving the context usable.
+ */
+hh_status hh_debug_fail_alloc(int k);
+hh_status hh_debug_wait_timeout(int64_t cycles, void *stream);
+
 /* Message for the last failed call on this host thread ("" if none). */
 const char *hh_last_error(void);
 

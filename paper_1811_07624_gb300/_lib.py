@@ -73,6 +73,8 @@ SIGNATURES = {
     "hh_tune_save": [ctypes.c_char_p],
     "hh_tune_load": [ctypes.c_char_p],
     "hh_tune_clear": [],
+    "hh_debug_fail_alloc": [ip],
+    "hh_debug_wait_timeout": [i64, vp],
 }
 
 # Functions that return a plain value, not an hh_status.

@@ -179,14 +179,14 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
     int *flag = nullptr;
     hh_status st = HH_OK;
     size_t es = dtype_size(dtype);
-    if ((e = cudaMalloc(&p->u, es * (size_t)p->ldv * (size_t)(h > 0 ? h : 1))) ||
-        (e = cudaMalloc(&p->tau, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
-        (e = cudaMalloc(&p->tau_t, es * (size_t)(h > 0 ? h : 1))) ||
-        (e = cudaMalloc(&p->gram, es * 16 * (size_t)(h > 0 ? h : 1))) ||
-        (e = cudaMalloc(&p->vnorm, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
-        (d && (e = cudaMalloc(&p->d, es * (size_t)p->ldv))) ||
-        (sign && (e = cudaMalloc(&p->sign, es * (size_t)p->ldv))) ||
-        (e = cudaMalloc(&p->err, sizeof(int))) || (e = cudaMalloc(&flag, sizeof(int)))) {
+    if ((e = dev_malloc(&p->u, es * (size_t)p->ldv * (size_t)(h > 0 ? h : 1))) ||
+        (e = dev_malloc(&p->tau, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
+        (e = dev_malloc(&p->tau_t, es * (size_t)(h > 0 ? h : 1))) ||
+        (e = dev_malloc(&p->gram, es * 16 * (size_t)(h > 0 ? h : 1))) ||
+        (e = dev_malloc(&p->vnorm, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
+        (d && (e = dev_malloc(&p->d, es * (size_t)p->ldv))) ||
+        (sign && (e = dev_malloc(&p->sign, es * (size_t)p->ldv))) ||
+        (e = dev_malloc(&p->err, sizeof(int))) || (e = dev_malloc(&flag, sizeof(int)))) {
         st = cuda_fail(e, "cudaMalloc (plan)");
         goto done;
     }

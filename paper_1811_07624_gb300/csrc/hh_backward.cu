@@ -487,7 +487,7 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
         void *buf = scratch;
         bool own = false;
         if (!buf) {
-            cudaError_t e = cudaMallocAsync(&buf, need, st);
+            cudaError_t e = dev_malloc_async(&buf, need, st);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (backward scratch)");
             own = true;
         } else if (need > scratch_bytes) {

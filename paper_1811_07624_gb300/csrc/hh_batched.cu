@@ -459,8 +459,8 @@ static hh_status batch_create(Batch **out, int count, const hh_plan_t *plans, co
 
     const size_t tbytes = sizeof(Task) * (size_t)(count > 0 ? count : 1);
     const size_t ibytes = sizeof(Item) * (size_t)(b->nitems > 0 ? b->nitems : 1);
-    if ((e = cudaMalloc(&b->d_tasks, tbytes)) || (e = cudaMalloc(&b->d_items, ibytes)) ||
-        (e = cudaMalloc(&b->d_counter, sizeof(int))) || (e = cudaMalloc(&b->d_err, sizeof(int))) ||
+    if ((e = dev_malloc(&b->d_tasks, tbytes)) || (e = dev_malloc(&b->d_items, ibytes)) ||
+        (e = dev_malloc(&b->d_counter, sizeof(int))) || (e = dev_malloc(&b->d_err, sizeof(int))) ||
         (e = cudaMallocHost(&b->pinned, tbytes)) ||
         (e = cudaEventCreateWithFlags(&b->upload_done, cudaEventDisableTiming)) ||
         (e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) ||
@@ -727,7 +727,7 @@ hh_status hh_tune(const int64_t *ns, int nn, const int64_t *hs, int nh, int64_t 
     hh_status st = HH_OK;
     const size_t vbytes = sizeof(float) * (size_t)std::max<int64_t>(hmax, 1) * nmax;
     const size_t xbytes = sizeof(float) * (size_t)rows * nmax;
-    if ((e = cudaMalloc(&U, vbytes)) || (e = cudaMalloc(&X, xbytes)) || (e = cudaMalloc(&Y, xbytes)) ||
+    if ((e = dev_malloc(&U, vbytes)) || (e = dev_malloc(&X, xbytes)) || (e = dev_malloc(&Y, xbytes)) ||
         (e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) {
         st = cuda_fail(e, "tune allocation");
         goto done;

@@ -50,6 +50,15 @@ struct Plan {
 hh_status fail(hh_status st, const char *fmt, ...);
 hh_status cuda_fail(cudaError_t e, const char *what);
 
+// Device allocations of the library go through these; the test hook
+// hh_debug_fail_alloc can make the k-th one fail (cudaErrorMemoryAllocation).
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+
 // A pointer the kernels of device `dev` may dereference (device or managed memory).
 bool device_ptr(const void *p, int dev);
 // The plan is non-null and belongs to the current device.

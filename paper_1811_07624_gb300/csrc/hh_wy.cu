@@ -503,14 +503,14 @@ hh_status wy_prepare(Plan *p, const void *U, int64_t ldu, const int8_t *sign, in
     cudaError_t e;
     const size_t bv = sizeof(__nv_bfloat16) * (size_t)w->hpad * w->n8;
     const size_t bvp = sizeof(__nv_bfloat16) * (size_t)w->P * n * w->PB;
-    if ((e = cudaMalloc(&w->Vb, bv)) || (sign && (e = cudaMalloc(&w->Vs, bv))) ||
-        (e = cudaMalloc(&w->Vp, bvp)) || (e = cudaMalloc(&w->Vpp, bvp)) ||
-        (sign && (e = cudaMalloc(&w->sign, sizeof(float) * n))) ||
-        (e = cudaMalloc(&w->V64, sizeof(double) * (size_t)w->hpad * n)) ||
-        (e = cudaMalloc(&w->G, sizeof(double) * (size_t)w->P * w->PB * w->PB)) ||
-        (e = cudaMalloc(&w->T, sizeof(double) * (size_t)w->P * w->PB * w->PB)) ||
-        (e = cudaFree(p->tau)) || (e = cudaMalloc(&p->tau, sizeof(double) * (size_t)w->hpad)) ||
-        (e = cudaFree(p->vnorm)) || (e = cudaMalloc(&p->vnorm, sizeof(double) * (size_t)w->hpad)))
+    if ((e = dev_malloc(&w->Vb, bv)) || (sign && (e = dev_malloc(&w->Vs, bv))) ||
+        (e = dev_malloc(&w->Vp, bvp)) || (e = dev_malloc(&w->Vpp, bvp)) ||
+        (sign && (e = dev_malloc(&w->sign, sizeof(float) * n))) ||
+        (e = dev_malloc(&w->V64, sizeof(double) * (size_t)w->hpad * n)) ||
+        (e = dev_malloc(&w->G, sizeof(double) * (size_t)w->P * w->PB * w->PB)) ||
+        (e = dev_malloc(&w->T, sizeof(double) * (size_t)w->P * w->PB * w->PB)) ||
+        (e = cudaFree(p->tau)) || (e = dev_malloc(&p->tau, sizeof(double) * (size_t)w->hpad)) ||
+        (e = cudaFree(p->vnorm)) || (e = dev_malloc(&p->vnorm, sizeof(double) * (size_t)w->hpad)))
         return cuda_fail(e, "cudaMalloc (compact-WY plan)");
     wy::wy_convert_kernel<<<(unsigned)w->hpad, 256, 0, st>>>(
         (const __nv_bfloat16 *)U, ldu, n, h, w->n8, sign, w->V64, w->Vb, w->Vs, p->tau, p->vnorm,

@@ -139,5 +139,5 @@ def test_module_trains():
         loss = ((model(X) - T) ** 2).mean()
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert losses[-1] < 0.5 * losses[0]

@@ -115,3 +115,10 @@ def test_batch_errors_without_device(L):
     assert _lib.STATUS[L.hh_batch_shape(-1, None, None, None, None, None)] == "HH_ERR_INVALID_ARG"
     st = L.hh_tune(None, 1, None, 1, 16, None)
     assert _lib.STATUS[st] == "HH_ERR_INVALID_ARG"
+
+
+def test_debug_hooks_argument_checks_without_device(L):
+    assert _lib.STATUS[L.hh_debug_fail_alloc(-1)] == "HH_ERR_INVALID_ARG"
+    assert L.hh_debug_fail_alloc(0) == 0
+    assert _lib.STATUS[L.hh_debug_wait_timeout(0, None)] == "HH_ERR_INVALID_ARG"
+    assert _lib.STATUS[L.hh_debug_wait_timeout(5_000_000_000, None)] == "HH_ERR_INVALID_ARG"
