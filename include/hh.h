@@ -102,9 +102,24 @@ hh_status hh_destroy(hh_plan_t plan);
 /*
  * Synchronise `stream` and report device-side failures of this plan's earlier
  * calls on it: HH_ERR_TIMEOUT if a kernel gave up a bounded wait (its output
- * is then incomplete), HH_OK otherwise.  Clears the plan's status word.
+ * is then incomplete), HH_ERR_INVALID_ARG for a pair index out of range
+ * (hh_mahalanobis), HH_ERR_NONFINITE for a NaN or Inf given to hh_update,
+ * HH_OK otherwise.  Clears the plan's status word.
  */
 hh_status hh_sync(hh_plan_t plan, void *stream);
+
+/*
+ * New reflector values for an existing F32 or F64 plan (§II-A: tau_k, the
+ * stored copies and the Gram band are recomputed in FP64 as at create): U is h
+ * rows of n device elements of the plan's dtype at U + k*ldu; d (n elements)
+ * must be given exactly when the plan was created with a spectrum, else NULL.
+ * The sign is kept.  Stream-ordered on `stream` with no allocation and no
+ * host synchronisation, so later calls on the same stream see the new values
+ * (for training loops: one plan, updated after each optimiser step).  A NaN or
+ * Inf in U or d is reported by the next hh_sync as HH_ERR_NONFINITE.  BF16
+ * (compact-WY) plans: HH_ERR_UNSUPPORTED; create a new plan.
+ */
+hh_status hh_update(hh_plan_t plan, const void *U, int64_t ldu, const void *d, void *stream);
 
 /* Shape and kernel family of a plan.  Any output pointer may be NULL. */
 hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype,

@@ -51,6 +51,7 @@ SIGNATURES = {
     "hh_create_ex": [ctypes.POINTER(vp), i64, i64, vp, i64, vp, vp, ip, ip, vp],
     "hh_destroy": [vp],
     "hh_sync": [vp, vp],
+    "hh_update": [vp, vp, i64, vp, vp],
     "hh_plan_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ip),
                      ctypes.POINTER(ip)],
     "hh_apply": [vp, vp, i64, vp, i64, i64, vp],

@@ -107,6 +107,22 @@ class Plan:
         """Wait for this plan's work on the stream; raise if a kernel timed out."""
         _lib.call("hh_sync", self._h, _stream_ptr(stream))
 
+    def update(self, U: torch.Tensor, d: torch.Tensor | None = None, stream=None) -> None:
+        """New reflector rows (and spectrum, if the plan has one) for this F32/F64
+        plan, stream-ordered, without allocation or host synchronisation."""
+        if U.shape != (self.h, self.n) or U.dtype != self.dtype or not U.is_cuda:
+            raise ValueError(f"U must be a CUDA {self.dtype} tensor of shape ({self.h}, {self.n})")
+        if self.h and U.stride(1) != 1:
+            raise ValueError("U rows must be contiguous")
+        ldu = U.stride(0) if self.h > 1 else self.n
+        dp = None
+        if d is not None:
+            if d.shape != (self.n,) or d.dtype != self.dtype or not d.is_cuda or d.stride(0) != 1:
+                raise ValueError(f"d must be a contiguous CUDA {self.dtype} tensor of shape ({self.n},)")
+            dp = d.data_ptr()
+        _lib.call("hh_update", self._h, U.data_ptr() if self.h else None, max(ldu, self.n), dp,
+                  _stream_ptr(stream))
+
     @property
     def handle(self) -> ctypes.c_void_p:
         return self._h

@@ -68,7 +68,11 @@ def mahalanobis(X: torch.Tensor, ia: torch.Tensor, ib: torch.Tensor, U: torch.Te
 
 class ReflectorTransform(torch.nn.Module):
     """h learnable reflector vectors (rows of ``U``) and an optional learnable
-    spectrum ``d``; ``forward(X, mode)`` applies the chain to the rows of X."""
+    spectrum ``d``; ``forward(X, mode)`` applies the chain to the rows of X.
+
+    The module keeps one plan and refreshes it in place (``hh_update``, no
+    allocation or host synchronisation) when its parameters have changed since
+    the last forward, e.g. after an optimiser step."""
 
     def __init__(self, n: int, h: int, spectrum: bool = True, sign: torch.Tensor | None = None,
                  dtype=torch.float32, device="cuda", generator=None):
@@ -77,6 +81,21 @@ class ReflectorTransform(torch.nn.Module):
         self.U = torch.nn.Parameter(U)
         self.d = torch.nn.Parameter(torch.ones(n, dtype=dtype, device=device)) if spectrum else None
         self.register_buffer("sign", None if sign is None else sign.to(device=device, dtype=torch.int8))
+        self._plan = None
+        self._plan_key = None
+
+    def plan(self) -> Plan:
+        """The plan for the current parameter values."""
+        U = self.U.detach()
+        d = None if self.d is None else self.d.detach()
+        key = (U.data_ptr(), U._version, None if d is None else (d.data_ptr(), d._version))
+        if self._plan is None or self._plan.dtype != U.dtype:
+            self._plan = Plan(U.contiguous(), d=d, sign=self.sign)
+        elif key != self._plan_key:
+            self._plan.update(U.contiguous(), d)
+        self._plan_key = key
+        return self._plan
 
     def forward(self, X: torch.Tensor, mode: str = "W") -> torch.Tensor:
-        return apply(X, self.U, self.d if mode == "SYM" else None, self.sign, mode)
+        plan = self.plan()
+        return _ChainFunction.apply(X, self.U, self.d if mode == "SYM" else None, plan, mode)

@@ -53,6 +53,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->gram);
     cudaFree(p->vnorm);
     cudaFree(p->err);
+    cudaFree(p->upd);
     delete p;
 }
 
@@ -186,7 +187,8 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
         (e = dev_malloc(&p->vnorm, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
         (d && (e = dev_malloc(&p->d, es * (size_t)p->ldv))) ||
         (sign && (e = dev_malloc(&p->sign, es * (size_t)p->ldv))) ||
-        (e = dev_malloc(&p->err, sizeof(int))) || (e = dev_malloc(&flag, sizeof(int)))) {
+        (e = dev_malloc(&p->err, sizeof(int))) || (e = dev_malloc(&p->upd, sizeof(int))) ||
+        (e = dev_malloc(&flag, sizeof(int)))) {
         st = cuda_fail(e, "cudaMalloc (plan)");
         goto done;
     }
@@ -195,7 +197,8 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
         goto done;
     }
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) ||
-        (e = cudaMemsetAsync(p->err, 0, sizeof(int), s))) {
+        (e = cudaMemsetAsync(p->err, 0, sizeof(int), s)) ||
+        (e = cudaMemsetAsync(p->upd, 0, sizeof(int), s))) {
         st = cuda_fail(e, "cudaMemsetAsync");
         goto done;
     }
@@ -255,8 +258,28 @@ hh_status hh_sync(hh_plan_t plan, void *stream) {
         return fail(HH_ERR_TIMEOUT, "a kernel's bounded wait on its bulk copy expired");
     if (word == HH_ERR_INVALID_ARG)
         return fail(HH_ERR_INVALID_ARG, "a pair index was outside [0, nrows)");
+    if (word == HH_ERR_NONFINITE)
+        return fail(HH_ERR_NONFINITE, "an update's U or d held a NaN or Inf");
     if (word != 0) return fail(HH_ERR_CUDA, "device status word %d", word);
     return HH_OK;
+}
+
+hh_status hh_update(hh_plan_t plan, const void *U, int64_t ldu, const void *d, void *stream) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    hh_status st = check_plan(p);
+    if (st) return st;
+    if (p->path != HH_PATH_FUSED)
+        return fail(HH_ERR_UNSUPPORTED, "update: F32 and F64 plans only (compact-WY: create anew)");
+    if (p->h > 0 && ldu < p->n)
+        return fail(HH_ERR_INVALID_ARG, "ldu = %lld < n = %lld", (long long)ldu, (long long)p->n);
+    if (p->h > 0 && !device_ptr(U, p->device))
+        return fail(HH_ERR_INVALID_ARG, "U: not a device pointer of device %d", p->device);
+    if ((d != nullptr) != (p->d != nullptr))
+        return fail(HH_ERR_INVALID_ARG, p->d ? "update: the plan has a spectrum, d is required"
+                                             : "update: the plan has no spectrum, d must be NULL");
+    if (d && !device_ptr(d, p->device))
+        return fail(HH_ERR_INVALID_ARG, "d: not a device pointer of device %d", p->device);
+    return update_fused(p, U, ldu, d, reinterpret_cast<cudaStream_t>(stream));
 }
 
 hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype, hh_path *path) {

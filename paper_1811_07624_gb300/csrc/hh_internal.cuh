@@ -41,6 +41,7 @@ struct Plan {
     double *tau = nullptr;  // h, tau_k = 2 / v_k^T v_k (0 for v_k = 0)
     double *vnorm = nullptr;// h, |v_k|
     int *err = nullptr;     // device status word: a kernel's bounded wait expired (HH_ERR_TIMEOUT)
+    int *upd = nullptr;     // device flag of the last hh_update's prepare kernels (bit 1: U, 2: d)
     int num_sms = 0;
     // WY path (BF16 storage): filled by wy_prepare
     void *wy = nullptr;
@@ -73,6 +74,9 @@ inline size_t dtype_size(hh_dtype t) {
 // Sets *nonfinite (device int) if U or d holds a NaN/Inf.
 hh_status prepare_fused(Plan *p, const void *U, int64_t ldu, const void *d, const int8_t *sign,
                         int *bad_flag, cudaStream_t st);
+// New reflector values (and spectrum) for an existing F32/F64 plan, stream-ordered,
+// no allocation: a NaN or Inf becomes HH_ERR_NONFINITE in the status word.
+hh_status update_fused(Plan *p, const void *U, int64_t ldu, const void *d, cudaStream_t st);
 
 // ---- compact-WY path on the tensor cores (hh_wy.cu), BF16 plans ----
 hh_status wy_prepare(Plan *p, const void *U, int64_t ldu, const int8_t *sign, int *flag,

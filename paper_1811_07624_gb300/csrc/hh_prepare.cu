@@ -115,7 +115,40 @@ hh_status prepare_typed(Plan *p, const void *U, int64_t ldu, const void *d, cons
     return HH_OK;
 }
 
+// After an update: a NaN or Inf seen by the prepare kernels (bits 1, 2 of
+// *upd) becomes HH_ERR_NONFINITE in the status word, unless an earlier error
+// is there; the flag is cleared for the next update.
+__global__ void update_status_kernel(int *upd, int *err) {
+    if (*upd & 3) atomicCAS(err, 0, (int)HH_ERR_NONFINITE);
+    *upd = 0;
+}
+
+template <typename T>
+hh_status update_typed(Plan *p, const void *U, int64_t ldu, const void *d, cudaStream_t st) {
+    if (p->h > 0) {
+        prepare_reflectors_kernel<T, T><<<(unsigned)p->h, kPrepThreads, 0, st>>>(
+            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, (T *)p->tau_t, p->vnorm, p->upd);
+        prepare_gram_kernel<T><<<dim3((unsigned)p->h, 16), kPrepThreads, 0, st>>>(
+            (const T *)p->u, p->ldv, p->n, p->h, (T *)p->gram);
+    }
+    if (d) {  // the sign is kept: no sign input, no sign output
+        int blocks = (int)((p->ldv + 255) / 256);
+        prepare_vectors_kernel<T, T><<<blocks, 256, 0, st>>>((const T *)d, nullptr, p->n, p->ldv,
+                                                             (T *)p->d, nullptr, p->upd);
+    }
+    update_status_kernel<<<1, 1, 0, st>>>(p->upd, p->err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "update kernels");
+    return HH_OK;
+}
+
 }  // namespace
+
+hh_status update_fused(Plan *p, const void *U, int64_t ldu, const void *d, cudaStream_t st) {
+    if (p->dtype == HH_F32) return update_typed<float>(p, U, ldu, d, st);
+    if (p->dtype == HH_F64) return update_typed<double>(p, U, ldu, d, st);
+    return fail(HH_ERR_UNSUPPORTED, "update: F32 and F64 plans only");
+}
 
 hh_status prepare_fused(Plan *p, const void *U, int64_t ldu, const void *d, const int8_t *sign,
                         int *flag, cudaStream_t st) {
