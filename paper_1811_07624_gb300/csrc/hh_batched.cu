@@ -78,7 +78,7 @@ struct Item {
 // item's task, tile and tiles left).
 extern __shared__ __align__(128) float b_stage[];
 __shared__ __align__(8) uint64_t b_full_bar;
-__shared__ float b_red[kRedFloats];
+__shared__ __align__(16) float b_red[kRedFloats];
 __shared__ int b_task[2];
 __shared__ long long b_tile[2];
 __shared__ int b_aborted;
@@ -120,6 +120,125 @@ __device__ __forceinline__ void issue_copy(const Task *__restrict__ tasks, int t
     } else {
         for (int r = 0; r < nvalid; ++r)
             staged::bulk_g2s(b_stage + (size_t)r * tk.n, src + r * tk.ldx, row_bytes, &b_full_bar);
+    }
+}
+
+// The chain of h reflectors on the RT rows in x, ascending or descending, in
+// blocks of kB with the Gram correction (the arithmetic of the staged kernel's
+// chain).  Granule indices i >= act (warp-uniform: the warp's columns there lie
+// past n) are neither read nor computed.  Per block: the reflector values and
+// tau are read at the block start, the dot products use one packed
+// accumulator per row, the kB * RT sums are reduced by one transposing warp
+// shuffle and one cross-warp combine, and the Gram entries are read after the
+// barrier (the shapes here hold more state per thread than the single-transform
+// kernel, and this order measured fastest for them).
+template <int G, int NG, int RT>
+__device__ __forceinline__ void tile_chain(float2 (&x)[RT][NG * 2], bool asc, int h,
+                                           const float *__restrict__ V, int64_t ldv,
+                                           const float *__restrict__ tau,
+                                           const float *__restrict__ gram, int t, int lane, int warp,
+                                           int rg, float *red, int &buf, int act) {
+    constexpr int RG = kThreads / G;
+    using C = staged::SCfg<G, NG, RT, RG, kB>;
+    constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L;
+    constexpr int KB = C::KEEP ? kB : 1;
+    for (int s = 0; s < h; s += kB) {
+        const int nb = h - s < kB ? h - s : kB;
+        int kk[kB];
+        float tk[kB];
+#pragma unroll
+        for (int j = 0; j < kB; ++j) {
+            kk[j] = asc ? s + j : h - 1 - s - j;
+            tk[j] = j < nb ? __ldg(tau + kk[j]) : 0.f;
+        }
+        float2 u[KB][E2];
+        auto load_u = [&](int j, float2(&dst)[E2]) {
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < nb && i < act)
+                    q = __ldg(reinterpret_cast<const float4 *>(V + (size_t)kk[j] * ldv) + (t + G * i));
+                dst[2 * i] = make_float2(q.x, q.y);
+                dst[2 * i + 1] = make_float2(q.z, q.w);
+            }
+        };
+        if constexpr (C::KEEP) {
+#pragma unroll
+            for (int j = 0; j < kB; ++j) load_u(j, u[j]);
+        }
+        float p[NV];
+#pragma unroll
+        for (int j = 0; j < kB; ++j) {
+            if constexpr (!C::KEEP) load_u(j, u[0]);
+            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
+            float2 a[RT];
+#pragma unroll
+            for (int r = 0; r < RT; ++r) a[r] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                if (i >= act) break;
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    a[r] = __ffma2_rn(x[r][2 * i], uj[2 * i], a[r]);
+                    a[r] = __ffma2_rn(x[r][2 * i + 1], uj[2 * i + 1], a[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RT; ++r) p[j * RT + r] = a[r].x + a[r].y;
+        }
+        float v = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
+        float z[NV];
+        if constexpr (NW == 1) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) z[q] = __shfl_sync(0xffffffffu, v, q * L);
+        } else {
+            if ((lane & (L - 1)) == 0) red[fused::red_index<RG, NV, NW>(buf, rg, lane / L, warp)] = v;
+            if constexpr (RG > 1)
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "n"(G) : "memory");
+            else
+                __syncthreads();
+            const int idx = lane / L, sub = lane & (L - 1);
+            float q = 0.f;
+#pragma unroll
+            for (int w = sub; w < NW; w += L) q += red[fused::red_index<RG, NV, NW>(buf, rg, idx, w)];
+#pragma unroll
+            for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+#pragma unroll
+            for (int qq = 0; qq < NV; ++qq) z[qq] = __shfl_sync(0xffffffffu, q, qq * L);
+            buf ^= 1;
+        }
+        float c[kB][RT];
+#pragma unroll
+        for (int j = 0; j < kB; ++j)
+#pragma unroll
+            for (int r = 0; r < RT; ++r) c[j][r] = z[j * RT + r];
+#pragma unroll
+        for (int j = 0; j < kB; ++j) {
+#pragma unroll
+            for (int r = 0; r < RT; ++r) c[j][r] *= -tk[j];
+#pragma unroll
+            for (int i = j + 1; i < kB; ++i) {
+                const int lo = asc ? kk[j] : kk[i];
+                const float g = i < nb ? __ldg(gram + (size_t)lo * staged::kGramBand + (i - j)) : 0.f;
+#pragma unroll
+                for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], g, c[i][r]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kB; ++j) {
+            if constexpr (!C::KEEP) load_u(j, u[0]);
+            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                if (i >= act) break;
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    const float2 cc = make_float2(c[j][r], c[j][r]);
+                    x[r][2 * i] = __ffma2_rn(uj[2 * i], cc, x[r][2 * i]);
+                    x[r][2 * i + 1] = __ffma2_rn(uj[2 * i + 1], cc, x[r][2 * i + 1]);
+                }
+            }
+        }
     }
 }
 
@@ -176,8 +295,8 @@ __device__ __noinline__ int tile_body(const Task *__restrict__ tasks, int slot, 
     for (int half = 0; half < (mode == HH_MODE_SYM ? 2 : 1); ++half) {
         if (half == 1) staged::scale2_part<G, NG, RT, RG, kB>(x, tk.d, t, act);
         const bool asc = mode != HH_MODE_W && half == 0;
-        staged::chain<G, NG, RT, RG, kB, true>(x, asc, tk.h, tk.V, tk.ldv, tk.tau, tk.gram, t,
-                                               lane, warp, rg, b_red, buf, act);
+        tile_chain<G, NG, RT>(x, asc, tk.h, tk.V, tk.ldv, tk.tau, tk.gram, t, lane, warp, rg, b_red,
+                              buf, act);
     }
     if (mode != HH_MODE_WT && sign) staged::scale2_part<G, NG, RT, RG, kB>(x, sign, t, act);
 

@@ -2,10 +2,27 @@
 // the number of columns n; COVER = G * NG * 4 columns per row group.
 #include "hh_staged.cuh"
 
-// Tuned (G, NG, RT, RG, B) of the n <= 4096 staged configuration.
+// Measured (G, NG, RT, RG, B) of the staged configurations for n <= 1024,
+// n <= 2048 and n <= 4096 (overridable at compile time for tuning runs).  The
+// n <= 1024 and n <= 4096 shapes are wide tiles (32 columns x 4 rows per
+// thread, up to 255 registers, 8 warps per SM).
+#ifndef HH_N1024_G
+#define HH_N1024_G 32
+#define HH_N1024_NG 8
+#define HH_N1024_RT 4
+#define HH_N1024_RG 4
+#define HH_N1024_B 2
+#endif
+#ifndef HH_N2048_G
+#define HH_N2048_G 128
+#define HH_N2048_NG 4
+#define HH_N2048_RT 4
+#define HH_N2048_RG 1
+#define HH_N2048_B 2
+#endif
 #ifndef HH_N4096_G
-#define HH_N4096_G 256
-#define HH_N4096_NG 4
+#define HH_N4096_G 128
+#define HH_N4096_NG 8
 #define HH_N4096_RT 4
 #define HH_N4096_RG 1
 #define HH_N4096_B 2
@@ -26,12 +43,13 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
     staged::launch<G, NG, RT, RG, B>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, \
                                      d, err, num_sms, st)
         // (G, NG, RT, RG, B): 4 rows per thread where the register budget allows,
-        // so each loaded reflector value feeds 8 FMAs; B reflectors per round.
+        // so each loaded reflector value feeds 8 FMAs; B reflectors per round;
+        // 32 columns per thread where n is large enough to fill them.
         if (n <= 128) return HH_STAGED(32, 1, 8, 4, 2);
         if (n <= 256) return HH_STAGED(32, 2, 8, 4, 2);
         if (n <= 512) return HH_STAGED(32, 4, 4, 4, 2);
-        if (n <= 1024) return HH_STAGED(64, 4, 4, 1, 2);
-        if (n <= 2048) return HH_STAGED(128, 4, 4, 1, 2);
+        if (n <= 1024) return HH_STAGED(HH_N1024_G, HH_N1024_NG, HH_N1024_RT, HH_N1024_RG, HH_N1024_B);
+        if (n <= 2048) return HH_STAGED(HH_N2048_G, HH_N2048_NG, HH_N2048_RT, HH_N2048_RG, HH_N2048_B);
         if (n <= 4096) return HH_STAGED(HH_N4096_G, HH_N4096_NG, HH_N4096_RT, HH_N4096_RG, HH_N4096_B);
         return HH_STAGED(512, 4, 2, 1, 2);
 #undef HH_STAGED

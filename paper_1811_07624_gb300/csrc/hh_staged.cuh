@@ -17,9 +17,12 @@
 // the previous tile is computed; reflector values are read through L1.
 //
 // Layout.  Persistent CTAs, as many per SM as fit.  A CTA is RG row groups of
-// G threads (RG > 1 only with one-warp groups); thread t of a group owns
+// G threads, each group with its own barrier; thread t of a group owns
 // granules t + G*i (i < NG) of 4 floats of each of its RT rows, so one loaded
 // reflector value feeds 2*RT FMAs.  Pairs of columns use the packed FP32 FMA.
+// Wide tiles (32 columns x 4 rows per thread) double the arithmetic per
+// shuffle reduction and per barrier; they need up to 255 registers, so they
+// run with half the resident warps.
 //
 // Waits on the mbarrier are bounded (about a second of clock cycles).  On
 // expiry the kernel records HH_ERR_TIMEOUT in *err, waits once more (bounded)
@@ -96,7 +99,15 @@ struct SCfg {
     static constexpr int COVER = G * E;   // columns covered
     static constexpr int NV = B * RT;     // dot products reduced together
     static constexpr int L = 32 / NV;     // lanes holding one value after the warp reduction
-    static constexpr bool KEEP = B * E <= 32;  // keep the block's reflector values in registers
+    // Wide tiles (32 columns x 4 or more rows per thread) run with up to 255
+    // registers per thread: fewer warps, each with twice the work per shuffle
+    // reduction and per barrier.  Other tiles are capped at 128 registers so
+    // that 16 warps stay resident.
+    static constexpr bool WIDE = E >= 32 && RT >= 4;
+    static constexpr int MINB = WIDE ? (256 / THREADS > 0 ? 256 / THREADS : 1)
+                                     : (512 / THREADS > 0 ? 512 / THREADS : 1);
+    // keep the block's reflector values in registers between dot and update
+    static constexpr bool KEEP = B * E <= (WIDE ? 64 : 32);
     static_assert(G % 32 == 0, "G must be a multiple of 32");
     static_assert(NV <= 32 && (NV & (NV - 1)) == 0, "B*RT must be a power of two <= 32");
     static_assert(B >= 1 && B <= kGramBand, "block larger than the stored Gram band");
@@ -117,8 +128,8 @@ __device__ __forceinline__ void scale2(float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E
     }
 }
 
-// Scale the columns of the held rows by s; with SKIP, only the first `act`
-// granule indices (warp-uniform) are touched.
+// Scale the columns of the held rows by s; only the first `act` granule
+// indices (a warp-uniform count) are touched.
 template <int G, int NG, int RT, int RG, int B>
 __device__ __forceinline__ void scale2_part(float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E2],
                                             const float *__restrict__ s, int t, int act) {
@@ -136,77 +147,74 @@ __device__ __forceinline__ void scale2_part(float2 (&x)[RT][SCfg<G, NG, RT, RG, 
 }
 
 // Apply h reflectors to the RT rows in x, ascending (k = 0..h-1) or descending
-// (k = h-1..0), in blocks of B.  With SKIP, granule indices i >= act (a
-// warp-uniform count: the warp's columns there lie past n) are neither read
-// nor computed.
-template <int G, int NG, int RT, int RG, int B, bool SKIP = false>
+// (k = h-1..0), in blocks of B.
+template <int G, int NG, int RT, int RG, int B>
 __device__ __forceinline__ void chain(
     float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E2], bool asc, int h, const float *__restrict__ V,
     int64_t ldv, const float *__restrict__ tau, const float *__restrict__ gram, int t, int lane,
-    int warp, int rg, float *red, int &buf, int act = NG) {
+    int warp, int rg, float *red, int &buf) {
     using C = SCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L;
-    for (int s = 0; s < h; s += B) {
-        const int nb = h - s < B ? h - s : B;
-        int kk[B];
-        float tk[B];
+    // Values of reflector j of the block starting at s (zeros past h).
+    auto load_block_u = [&](int s0, int j, float2(&dst)[E2]) {
+        const bool ok = s0 + j < h;
+        const int k = asc ? s0 + j : h - 1 - s0 - j;
+        const float4 *row = reinterpret_cast<const float4 *>(V + (size_t)(ok ? k : 0) * ldv);
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) q = __ldg(row + (t + G * i));
+            dst[2 * i] = make_float2(q.x, q.y);
+            dst[2 * i + 1] = make_float2(q.z, q.w);
+        }
+    };
+    // Reflector values: all B kept in registers between the dot and the
+    // update phase (KEEP), or one at a time and read again for the update.
+    // Kept values are software-pipelined: reflector j of the next block is
+    // loaded as soon as the update with reflector j of this block is issued,
+    // so its latency hides behind the rest of the update instead of stalling
+    // the next block's dot products.
+    constexpr int KB = C::KEEP ? B : 1;
+    float2 u[KB][E2];
+    if constexpr (C::KEEP) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) load_block_u(0, j, u[j]);
+    }
+    // tau and the Gram entries of the block starting at s0 (zeros past h),
+    // read before the block's reduction so that their latency is not exposed
+    // between the barrier and the update.
+    auto load_coef = [&](int s0, float(&tk)[B], float(&gv)[B][B]) {
+        const int nb0 = h - s0 < B ? h - s0 : B;
 #pragma unroll
         for (int j = 0; j < B; ++j) {
-            kk[j] = asc ? s + j : h - 1 - s - j;
-            tk[j] = j < nb ? __ldg(tau + kk[j]) : 0.f;
-        }
-        // Reflector values: all B kept in registers between the dot and the
-        // update phase (KEEP), or one at a time and read again for the update.
-        constexpr int KB = C::KEEP ? B : 1;
-        float2 u[KB][E2];
-        auto load_u = [&](int j, float2(&dst)[E2]) {
+            const int kj = asc ? s0 + j : h - 1 - s0 - j;
+            tk[j] = j < nb0 ? __ldg(tau + kj) : 0.f;
 #pragma unroll
-            for (int i = 0; i < NG; ++i) {
-                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < nb && (!SKIP || i < act))
-                    q = __ldg(reinterpret_cast<const float4 *>(V + (size_t)kk[j] * ldv) + (t + G * i));
-                dst[2 * i] = make_float2(q.x, q.y);
-                dst[2 * i + 1] = make_float2(q.z, q.w);
+            for (int i = 0; i < B; ++i) {
+                const int ki = asc ? s0 + i : h - 1 - s0 - i;
+                gv[j][i] = (i > j && i < nb0)
+                               ? __ldg(gram + (size_t)(asc ? kj : ki) * kGramBand + (i - j))
+                               : 0.f;
             }
-        };
-        if constexpr (C::KEEP) {
-#pragma unroll
-            for (int j = 0; j < B; ++j) load_u(j, u[j]);
         }
+    };
+    for (int s = 0; s < h; s += B) {
+        const int nb = h - s < B ? h - s : B;
+        float tk[B], gv[B][B];
+        load_coef(s, tk, gv);
+        auto load_u = [&](int j, float2(&dst)[E2]) { load_block_u(s, j, dst); };
         float p[NV];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             if constexpr (!C::KEEP) load_u(j, u[0]);
             const float2(&uj)[E2] = u[C::KEEP ? j : 0];
-            if constexpr (SKIP) {
-                // granule-major, so one warp-uniform test per granule; one
-                // packed accumulator per row
-                float2 a[RT];
+            // one packed accumulator per row
 #pragma unroll
-                for (int r = 0; r < RT; ++r) a[r] = make_float2(0.f, 0.f);
+            for (int r = 0; r < RT; ++r) {
+                float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < NG; ++i) {
-                    if (i >= act) break;
-#pragma unroll
-                    for (int r = 0; r < RT; ++r) {
-                        a[r] = __ffma2_rn(x[r][2 * i], uj[2 * i], a[r]);
-                        a[r] = __ffma2_rn(x[r][2 * i + 1], uj[2 * i + 1], a[r]);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < RT; ++r) p[j * RT + r] = a[r].x + a[r].y;
-            } else {
-#pragma unroll
-                for (int r = 0; r < RT; ++r) {
-                    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int e = 0; e < E2; e += 2) {
-                        a = __ffma2_rn(x[r][e], uj[e], a);
-                        if (e + 1 < E2) b = __ffma2_rn(x[r][e + 1], uj[e + 1], b);
-                    }
-                    a = __fadd2_rn(a, b);
-                    p[j * RT + r] = a.x + a.y;
-                }
+                for (int e = 0; e < E2; ++e) a = __ffma2_rn(x[r][e], uj[e], a);
+                p[j * RT + r] = a.x + a.y;
             }
         }
         float v = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
@@ -247,35 +255,21 @@ __device__ __forceinline__ void chain(
             for (int r = 0; r < RT; ++r) c[j][r] *= -tk[j];
 #pragma unroll
             for (int i = j + 1; i < B; ++i) {
-                const int lo = asc ? kk[j] : kk[i];
-                const float g = i < nb ? __ldg(gram + (size_t)lo * kGramBand + (i - j)) : 0.f;
 #pragma unroll
-                for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], g, c[i][r]);
+                for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], gv[j][i], c[i][r]);
             }
         }
 #pragma unroll
         for (int j = 0; j < B; ++j) {
             if constexpr (!C::KEEP) load_u(j, u[0]);
             const float2(&uj)[E2] = u[C::KEEP ? j : 0];
-            if constexpr (SKIP) {
 #pragma unroll
-                for (int i = 0; i < NG; ++i) {
-                    if (i >= act) break;
+            for (int r = 0; r < RT; ++r) {
+                const float2 cc = make_float2(c[j][r], c[j][r]);
 #pragma unroll
-                    for (int r = 0; r < RT; ++r) {
-                        const float2 cc = make_float2(c[j][r], c[j][r]);
-                        x[r][2 * i] = __ffma2_rn(uj[2 * i], cc, x[r][2 * i]);
-                        x[r][2 * i + 1] = __ffma2_rn(uj[2 * i + 1], cc, x[r][2 * i + 1]);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < RT; ++r) {
-                    const float2 cc = make_float2(c[j][r], c[j][r]);
-#pragma unroll
-                    for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
-                }
+                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
             }
+            if constexpr (C::KEEP) load_block_u(s + B, j, u[j]);
         }
     }
 }
@@ -283,9 +277,10 @@ __device__ __forceinline__ void chain(
 // Requirements (checked by the launcher): n % 4 == 0, n <= COVER, X and Y rows
 // and bases 16-byte aligned, V rows padded with zeros to ldv >= COVER, ldv % 4
 // == 0, ROWS*n floats of dynamic shared memory.
-// At least 16 resident warps per SM: caps registers at 128 per thread.
+// Registers: at most 128 per thread (16 resident warps per SM), or 255 for wide
+// tiles (8 warps per SM).
 template <int MODE, int G, int NG, int RT, int RG, int B>
-__global__ void __launch_bounds__(G *RG, (512 / (G * RG)) > 0 ? 512 / (G * RG) : 1)
+__global__ void __launch_bounds__(G *RG, (SCfg<G, NG, RT, RG, B>::MINB))
 staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t batch, int n,
                     const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv,
                     int h, const float *__restrict__ gram, const float *__restrict__ sign,
@@ -294,7 +289,7 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
     constexpr int E2 = C::E2, ROWS = C::ROWS;
     extern __shared__ __align__(128) float stage[];  // ROWS x n
     __shared__ __align__(8) uint64_t full_bar;
-    __shared__ float red[2 * RG * C::NV * C::NW];
+    __shared__ __align__(16) float red[2 * RG * C::NV * C::NW];
     __shared__ int aborted;
 
     const int tid = threadIdx.x;
