@@ -110,7 +110,7 @@ def test_f32_reflector_counts(h):
 
 @pytest.mark.parametrize("batch", [0, 1, 2, 7, 8, 9, 31, 33, 513])
 def test_batch_tails(batch):
-    for n in (256, 4096):
+    for n in (256, 1000, 4096):
         for mode in ("W", "SYM"):
             _check(mode, n, 6, batch, torch.float32, seed=batch)
 
