@@ -289,6 +289,43 @@ def test_mahalanobis_matches_quadratic_form():
     assert rel(out0, (delta ** 2) @ d) < 1e-15
 
 
+def test_mahalanobis_gradient_composition_central_differences():
+    # The gradient reference of the GPU tests for the distance of §IV-C: with
+    # z_p = W^T(sigma .* delta_p) and L = sum_p g_p sum_m d_m z_pm^2,
+    # dL/dd = sum_p g_p z_p .* z_p and dL/dU is the W^T adjoint seeded with
+    # 2 g_p d .* z_p.  Pinned here against central differences of the distance.
+    n, h = 6, 3
+    U = si.reflectors(n, h, seed=61, unit=False)
+    d = si.spectrum(n, seed=61)
+    s = si.sign(n, seed=61)
+    X = si.vectors(5, n, seed=61)
+    ia, ib = np.array([0, 1, 2, 4]), np.array([1, 3, 0, 2])
+    g = np.random.default_rng(61).standard_normal(ia.shape[0])
+    delta = X[ia] - X[ib]
+    z = oracle.apply("WT", U, delta, sign=s)
+    gd_ref = (g[:, None] * z * z).sum(axis=0)
+    _, gU_ref, _ = oracle.backward("WT", U, delta, 2.0 * g[:, None] * d[None, :] * z, sign=s)
+
+    def f(U_, d_):
+        return float(g @ oracle.mahalanobis(U_, X, ia, ib, d_, sign=s))
+
+    eps = 1e-6
+    num_U = np.zeros_like(U)
+    for idx in np.ndindex(U.shape):
+        Up, Um = U.copy(), U.copy()
+        Up[idx] += eps
+        Um[idx] -= eps
+        num_U[idx] = (f(Up, d) - f(Um, d)) / (2 * eps)
+    num_d = np.zeros_like(d)
+    for i in range(n):
+        dp, dm = d.copy(), d.copy()
+        dp[i] += eps
+        dm[i] -= eps
+        num_d[i] = (f(U, dp) - f(U, dm)) / (2 * eps)
+    assert rel(gU_ref, num_U) < 1e-7
+    assert rel(gd_ref, num_d) < 1e-7
+
+
 def test_invalid_arguments():
     with pytest.raises(ValueError):
         oracle.apply("SYM", np.ones((1, 4)), np.ones((1, 4)))  # SYM without d
