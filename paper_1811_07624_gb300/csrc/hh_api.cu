@@ -140,6 +140,7 @@ hh_status hh_create(hh_plan_t *out, int64_t n, int64_t h, const void *U, int64_t
 hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int64_t ldu,
                        const void *d, const int8_t *sign, hh_dtype dtype, hh_path path,
                        void *stream) {
+    TraceRange trace("hh_create_ex");
     if (!out) return fail(HH_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1) return fail(HH_ERR_INVALID_ARG, "n = %lld < 1", (long long)n);
@@ -265,6 +266,7 @@ hh_status hh_sync(hh_plan_t plan, void *stream) {
 }
 
 hh_status hh_update(hh_plan_t plan, const void *U, int64_t ldu, const void *d, void *stream) {
+    TraceRange trace("hh_update");
     Plan *p = reinterpret_cast<Plan *>(plan);
     hh_status st = check_plan(p);
     if (st) return st;
@@ -294,22 +296,26 @@ hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype, 
 
 hh_status hh_apply(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
                    int64_t batch, void *stream) {
+    TraceRange trace("hh_apply");
     return apply_common(plan, HH_MODE_W, X, ldx, Y, ldy, batch, stream);
 }
 
 hh_status hh_apply_T(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
                      int64_t batch, void *stream) {
+    TraceRange trace("hh_apply_T");
     return apply_common(plan, HH_MODE_WT, X, ldx, Y, ldy, batch, stream);
 }
 
 hh_status hh_apply_sym(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
                        int64_t batch, void *stream) {
+    TraceRange trace("hh_apply_sym");
     return apply_common(plan, HH_MODE_SYM, X, ldx, Y, ldy, batch, stream);
 }
 
 hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t lds,
                       const void *gY, int64_t ldgy, void *gX, int64_t ldgx, void *gU, void *gd,
                       int64_t batch, void *stream) {
+    TraceRange trace("hh_backward");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     hh_status st = check_backward_args(p, mode, saved, lds, gY, ldgy, gX, ldgx, gU, gd, batch);
     if (st) return st;
@@ -338,6 +344,7 @@ static hh_status check_pairs(const Plan *p, const void *X, int64_t ldx, int64_t 
 hh_status hh_mahalanobis(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
                          const int64_t *ia, const int64_t *ib, int64_t npairs, void *out,
                          void *stream) {
+    TraceRange trace("hh_mahalanobis");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     hh_status st = check_pairs(p, X, ldx, nrows, ia, ib, npairs);
     if (st) return st;
@@ -351,6 +358,7 @@ hh_status hh_mahalanobis(hh_plan_t plan, const void *X, int64_t ldx, int64_t nro
 hh_status hh_mahalanobis_backward(hh_plan_t plan, const void *X, int64_t ldx, int64_t nrows,
                                   const int64_t *ia, const int64_t *ib, int64_t npairs,
                                   const void *gout, void *gU, void *gd, void *stream) {
+    TraceRange trace("hh_mahalanobis_backward");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     hh_status st = check_pairs(p, X, ldx, nrows, ia, ib, npairs);
     if (st) return st;

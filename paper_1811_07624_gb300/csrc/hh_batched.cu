@@ -694,6 +694,7 @@ hh_status hh_batch_create(hh_batch_t *out, int count, const hh_plan_t *plans,
 
 hh_status hh_batch_apply(hh_batch_t batch, hh_mode mode, const void *const *X, const int64_t *ldx,
                          void *const *Y, const int64_t *ldy, void *stream) {
+    TraceRange trace("hh_batch_apply");
     return batch_apply(reinterpret_cast<Batch *>(batch), (int)mode, X, ldx, Y, ldy,
                        reinterpret_cast<cudaStream_t>(stream));
 }
@@ -825,6 +826,7 @@ hh_status hh_tune_load(const char *path) {
 
 hh_status hh_tune(const int64_t *ns, int nn, const int64_t *hs, int nh, int64_t rows,
                   void *stream) {
+    TraceRange trace("hh_tune");
     using namespace batched;
     if (nn < 0 || nh < 0 || (nn > 0 && !ns) || (nh > 0 && !hs))
         return fail(HH_ERR_INVALID_ARG, "ns/hs arrays");

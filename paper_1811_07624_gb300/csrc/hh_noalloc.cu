@@ -47,6 +47,7 @@ extern "C" hh_status hh_backward_noalloc(hh_plan_t plan, hh_mode mode, const voi
                                          int64_t lds, const void *gY, int64_t ldgy, void *gX,
                                          int64_t ldgx, void *gU, void *gd, int64_t batch,
                                          void *stream) {
+    TraceRange trace("hh_backward_noalloc");
     const Plan *p = reinterpret_cast<const Plan *>(plan);
     hh_status st = check_backward_args(p, mode, saved, lds, gY, ldgy, gX, ldgx, gU, gd, batch);
     if (st) return st;

@@ -9,7 +9,11 @@
   a hinge loss on labelled pairs of a 10-class mixture in n = 256 whose noise
   has wide directions; the loss falls and 1-NN accuracy with the learned metric
   is no worse than Euclidean on held-out points.
-Both run every forward and backward through the library's kernels (autograd).
+* Checkpoint and resume: a fit interrupted after N steps, saved (module and
+  optimiser state dicts, the probe generator's state, the step), restored into
+  fresh objects and continued for M steps retraces the uninterrupted N + M
+  steps (the kernels reduce in a fixed order, so the losses agree to rounding).
+All run every forward and backward through the library's kernels (autograd).
 """
 
 import numpy as np
@@ -89,3 +93,51 @@ def test_fit_mahalanobis_metric_hinge_loss():
     print(f"hinge loss {losses[0]:.3f} -> {losses[-1]:.3f}; 1-NN accuracy "
           f"Euclidean {acc_euclid:.3f}, learned {acc_learned:.3f}")
     assert acc_learned >= acc_euclid - 0.01
+
+
+def test_checkpoint_resume_matches_uninterrupted(tmp_path):
+    from paper_1811_07624_gb300 import ReflectorTransform
+
+    n, h, probes, N, M = 256, 8, 2048, 6, 5
+    S, _, _ = si.decaying_symmetric(n, seed=1)
+    St = torch.tensor(S, dtype=torch.float32, device=DEV)
+
+    def make():
+        g = torch.Generator(device=DEV).manual_seed(3)
+        model = ReflectorTransform(n, h, spectrum=True, generator=g)
+        return model, torch.optim.Adam(model.parameters(), lr=0.02)
+
+    def run(model, opt, gen, steps):
+        out = []
+        for _ in range(steps):
+            x = torch.randn(probes, n, device=DEV, generator=gen)
+            opt.zero_grad()
+            loss = ((x @ St - model(x, "SYM")) ** 2).sum(1).mean()
+            loss.backward()
+            opt.step()
+            out.append(float(loss.detach()))
+        return out
+
+    model, opt = make()
+    ref = run(model, opt, torch.Generator(device=DEV).manual_seed(11), N + M)
+
+    model1, opt1 = make()
+    gen1 = torch.Generator(device=DEV).manual_seed(11)
+    first = run(model1, opt1, gen1, N)
+    path = tmp_path / "fit.pt"
+    torch.save({"model": model1.state_dict(), "opt": opt1.state_dict(),
+                "rng": gen1.get_state(), "step": N}, path)
+    del model1, opt1, gen1
+
+    ck = torch.load(path)
+    model2, opt2 = make()
+    model2.load_state_dict(ck["model"])
+    opt2.load_state_dict(ck["opt"])
+    gen2 = torch.Generator(device=DEV)
+    gen2.set_state(ck["rng"])
+    assert ck["step"] == N
+    second = run(model2, opt2, gen2, M)
+    np.testing.assert_allclose(first + second, ref, rtol=1e-6)
+    with torch.no_grad():
+        for a, b in zip(model.parameters(), model2.parameters()):
+            torch.testing.assert_close(a, b, rtol=1e-5, atol=1e-6)
