@@ -80,6 +80,9 @@ class Plan:
                       _lib.DTYPES[_TORCH_DTYPES[U.dtype]], _lib.PATHS[path],
                       _stream_ptr(stream))
         self._h = handle
+        # incremented by update(): an autograd graph built before an update
+        # must not run its backward with the new reflector values
+        self.generation = 0
         n64, h64, dt, pa = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
         _lib.call("hh_plan_info", self._h, ctypes.byref(n64), ctypes.byref(h64),
                   ctypes.byref(dt), ctypes.byref(pa))
@@ -122,6 +125,7 @@ class Plan:
             dp = d.data_ptr()
         _lib.call("hh_update", self._h, U.data_ptr() if self.h else None, max(ldu, self.n), dp,
                   _stream_ptr(stream))
+        self.generation += 1
 
     @property
     def handle(self) -> ctypes.c_void_p:

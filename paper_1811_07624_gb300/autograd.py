@@ -15,17 +15,29 @@ import torch
 from .api import Plan
 
 
+def _check_generation(ctx):
+    # The plan holds the reflector values of the forward pass only until it is
+    # updated in place; a backward after that would use the new values.
+    if ctx.plan.generation != ctx.generation:
+        raise RuntimeError(
+            "the reflector plan was updated after this forward pass; its backward would use "
+            "the new reflector values (run backward before the next optimiser step, or use a "
+            "new plan)")
+
+
 class _ChainFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, U, d, plan, mode):
         Y = plan.apply_mode(mode, X.contiguous())
         ctx.plan = plan
+        ctx.generation = plan.generation
         ctx.mode = mode
         ctx.save_for_backward(X if mode == "SYM" else Y)
         return Y
 
     @staticmethod
     def backward(ctx, gY):
+        _check_generation(ctx)
         (saved,) = ctx.saved_tensors
         need_x, need_u, need_d = ctx.needs_input_grad[:3]
         gX, gU, gd = ctx.plan.backward(ctx.mode, saved, gY.contiguous(), need_gX=need_x,
@@ -46,11 +58,13 @@ class _MahalanobisFunction(torch.autograd.Function):
     def forward(ctx, X, U, d, plan, ia, ib):
         out = plan.mahalanobis(X.contiguous(), ia, ib)
         ctx.plan = plan
+        ctx.generation = plan.generation
         ctx.save_for_backward(X, ia, ib)
         return out
 
     @staticmethod
     def backward(ctx, gout):
+        _check_generation(ctx)
         X, ia, ib = ctx.saved_tensors
         gU, gd = ctx.plan.mahalanobis_backward(X.contiguous(), ia, ib, gout.contiguous(),
                                                need_gU=ctx.needs_input_grad[1],

@@ -68,9 +68,13 @@ hh_status hh_debug_wait_timeout(int64_t cycles, void *stream) {
     cudaError_t e;
     if ((e = cudaMallocAsync(reinterpret_cast<void **>(&d), sizeof(int), s))) return cuda_fail(e, "probe status");
     wait_probe_kernel<<<1, 32, 0, s>>>(cycles, d);
-    if ((e = cudaGetLastError()) || (e = cudaMemcpyAsync(&word, d, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
-        (e = cudaFreeAsync(d, s)) || (e = cudaStreamSynchronize(s)))
-        return cuda_fail(e, "wait probe");
+    if ((e = cudaGetLastError()) == cudaSuccess)
+        e = cudaMemcpyAsync(&word, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    // the status word is freed on every path once it was allocated
+    const cudaError_t ef = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe");
     if (word == HH_ERR_TIMEOUT)
         return fail(HH_ERR_TIMEOUT, "the bounded wait gave up after %lld cycles (expected)",
                     (long long)cycles);

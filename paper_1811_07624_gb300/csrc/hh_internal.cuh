@@ -7,6 +7,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include <mutex>
 #include <string>
 
 #include "hh.h"
@@ -23,6 +24,40 @@ struct TraceRange {
 };
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Device ordinals the library keeps per-device state for (kernel attributes,
+// occupancy, the no-allocation scratch address).
+constexpr int kMaxDevices = 64;
+
+// Once-per-device set-up of a kernel.  Attributes such as the dynamic
+// shared-memory opt-in are per-device settings, so the set-up runs the first
+// time each device ordinal launches the kernel (under a lock: launches may
+// come from several host threads) and its result, e.g. the resident CTAs per
+// SM measured with that opt-in, is cached under the same ordinal.
+struct PerDevice {
+    std::mutex mu;
+    int value[kMaxDevices] = {};
+    bool done[kMaxDevices] = {};
+};
+// Runs setup(int &value) -> cudaError_t on the current device's first call;
+// returns the cached value in `out`.
+template <typename F>
+cudaError_t per_device(PerDevice &pd, int &out, F &&setup) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(pd.mu);
+    if (!pd.done[dev]) {
+        int v = 0;
+        e = setup(v);
+        if (e != cudaSuccess) return e;
+        pd.value[dev] = v;
+        pd.done[dev] = true;
+    }
+    out = pd.value[dev];
+    return cudaSuccess;
+}
 
 // Row stride (elements) of every per-plan vector stored on the device: the
 // next power of two >= max(n, 1024) up to 16384, else n rounded up to 1024.

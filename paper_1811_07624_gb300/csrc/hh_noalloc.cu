@@ -16,14 +16,17 @@ constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
 // its own partial sums), so nothing left from an earlier call is used.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on device `dev` (the current device).
-// In host code the array's name is only a host-side stand-in, so the address
-// is looked up once per device with cudaGetSymbolAddress and cached.
-hh_status scratch_address(int dev, void **out) {
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device with cudaGetSymbolAddress (which resolves it on the current
+// device) and cached under that same device's ordinal.
+hh_status scratch_address(void **out) {
+    int dev = -1;
+    cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return cuda_fail(ed, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices)
         return fail(HH_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
     std::lock_guard<std::mutex> lock(g_mu);
@@ -53,7 +56,8 @@ extern "C" hh_status hh_backward_noalloc(hh_plan_t plan, hh_mode mode, const voi
     if (st) return st;
     if (batch == 0 && !gU && !gd) return HH_OK;
     void *scratch = nullptr;
-    if ((st = scratch_address(p->device, &scratch))) return st;
+    // check_backward_args has made sure the current device is the plan's
+    if ((st = scratch_address(&scratch))) return st;
     // backward() with a caller buffer never allocates: it lowers the number of
     // CTAs until their partial sums fit, and rejects the call if one CTA's do not.
     return backward(p, mode, saved, lds, gY, ldgy, gX, ldgx, gU, gd, batch, scratch,

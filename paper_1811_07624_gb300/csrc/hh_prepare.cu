@@ -3,8 +3,9 @@
 //
 // Reflector k is H_k = I - tau_k v_k v_k^T with tau_k = 2 / (v_k^T v_k)
 // (§II-A, Eq. (2) with u_k = v_k / |v_k|); tau_k = 0 when v_k = 0, so
-// H_k = I (§II-B).  The fused kernels read the pre-scaled vector
-// u'_k = sqrt(tau_k) v_k, for which H_k z = z - u'_k (u'_k . z).
+// H_k = I (§II-B).  The kernels read v_k as given (zero padded to the plan's
+// row stride) and apply H_k z = z - tau_k v_k (v_k . z); tau_k is stored
+// separately, in FP64 and rounded to the compute type.
 #include "hh_internal.cuh"
 
 namespace hh {

@@ -384,24 +384,25 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
     using C = SCfg<G, NG, RT, RG, B>;
     const size_t smem = (size_t)C::ROWS * n * sizeof(float);
     const int64_t tiles = (batch + C::ROWS - 1) / C::ROWS;
-    // Per kernel (one entry per mode): the shared-memory opt-in at the largest
-    // stage this configuration can need, and the resident CTAs per SM there
-    // (a lower bound for smaller stages), both set on first use.
-    static bool ready[3] = {false, false, false};
-    static int per_sm[3] = {0, 0, 0};
+    // Per kernel (one entry per mode) and device: the shared-memory opt-in at
+    // the largest stage this configuration can need, and the resident CTAs per
+    // SM there (a lower bound for smaller stages), both set on first use.
+    static PerDevice state[3];
     auto run = [&](auto kern) -> cudaError_t {
-        cudaError_t e;
-        if (!ready[mode]) {
+        int per_sm = 1;
+        cudaError_t e = per_device(state[mode], per_sm, [&](int &v) -> cudaError_t {
             const size_t smax = (size_t)C::ROWS * C::COVER * sizeof(float);
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-            if (e != cudaSuccess) return e;
+            cudaError_t e2 =
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            if (e2 != cudaSuccess) return e2;
             int nb = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::THREADS, smax);
-            if (e != cudaSuccess) return e;
-            per_sm[mode] = nb > 0 ? nb : 1;
-            ready[mode] = true;
-        }
-        const int64_t slots = (int64_t)num_sms * per_sm[mode];
+            e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::THREADS, smax);
+            if (e2 != cudaSuccess) return e2;
+            v = nb > 0 ? nb : 1;
+            return cudaSuccess;
+        });
+        if (e != cudaSuccess) return e;
+        const int64_t slots = (int64_t)num_sms * per_sm;
         const int grid = (int)(tiles < slots ? tiles : slots);
         kern<<<grid, C::THREADS, smem, st>>>(X, ldx, Y, ldy, batch, n, V, tau, ldv, h, gram, sign,
                                              d, err);

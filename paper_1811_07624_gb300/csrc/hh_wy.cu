@@ -187,6 +187,7 @@ struct Bars {
     uint64_t z_full;                                 // Z in tensor memory written
     uint64_t zs_full, zs_free;                       // Z as BF16 operand in tensor memory
     uint64_t acc_full[kNumAcc], acc_empty[kNumAcc];
+    uint64_t drain;                                  // every MMA of the CTA has completed
     uint32_t tbase;
     int aborted;
 };
@@ -240,6 +241,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         tc::mbar_init(&B.z_full, 1);
         tc::mbar_init(&B.zs_full, 4);
         tc::mbar_init(&B.zs_free, 1);
+        tc::mbar_init(&B.drain, 1);
         for (int c = 0; c < kNumAcc; ++c) {
             tc::mbar_init(&B.acc_full[c], 1);
             tc::mbar_init(&B.acc_empty[c], 4);
@@ -257,14 +259,18 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
     const uint32_t tz = B.tbase;
 
     // Bounded wait; after a timeout the kernel records HH_ERR_TIMEOUT and stops
-    // waiting (its results are then not to be trusted).
+    // waiting (its results are then not to be trusted).  The copy warps then
+    // stop issuing loads and the MMA warp stops issuing MMAs; before tensor
+    // memory is freed, each of them waits (bounded) for what it has in flight.
+    auto aborted = [&]() { return *(volatile int *)&B.aborted != 0; };
     auto wait = [&](uint64_t *bar, uint32_t parity) {
-        if (*(volatile int *)&B.aborted) return;
+        if (aborted()) return;
         if (!tc::mbar_wait(bar, parity)) {
             atomicExch(a.err, (int)HH_ERR_TIMEOUT);
             *(volatile int *)&B.aborted = 1;
         }
     };
+    constexpr uint32_t kNone = 0xffffffffu;
 
     // Order of the operand ring and of the MMAs, per tile i (tiles of this CTA
     // t_0, t_1, ...): GEMM 1 of t_0 alone; then for each tile, output chunk j
@@ -277,9 +283,13 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
         // ---- TMA producer: operand ring ----------------------------------------------------
         if (lane == 0) {
             uint32_t it = 0;
+            uint32_t last[kMaxStages];  // load index that last armed each stage
+            for (int s = 0; s < kMaxStages; ++s) last[s] = kNone;
             auto load1 = [&](int64_t tile, int kc) {
                 const uint32_t s = it % NS;
                 wait(&B.empty[s], ((it / NS) & 1) ^ 1);
+                if (aborted()) return;
+                last[s] = it;
                 unsigned char *st = ring + s * stage_bytes;
                 tc::mbar_expect_tx(&B.full[s], bytesX + bytesV);
                 tc::tma_load_2d(st, &mapX, kc * 64, (int)(tile * kTileM), &B.full[s]);
@@ -289,6 +299,8 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
             auto load2 = [&](int nc) {
                 const uint32_t s = it % NS;
                 wait(&B.empty[s], ((it / NS) & 1) ^ 1);
+                if (aborted()) return;
+                last[s] = it;
                 unsigned char *st = ring + s * stage_bytes;
                 tc::mbar_expect_tx(&B.full[s], (uint32_t)PB * 128);
                 for (int kb = 0; kb < PB / 64; ++kb)
@@ -298,26 +310,36 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
             };
             if (first < a.tiles)
                 for (int kc = 0; kc < KC; ++kc) load1(first, kc);
-            for (int64_t tile = first; tile < a.tiles; tile += step) {
+            for (int64_t tile = first; tile < a.tiles && !aborted(); tile += step) {
                 const bool next = tile + step < a.tiles;
                 for (int j = 0; j < steps; ++j) {
                     if (j < NC) load2(NC - 1 - j);
                     if (next && j < KC) load1(tile + step, j);
                 }
             }
+            // the last load of each stage has landed before the CTA ends (a
+            // no-op unless the kernel gave up a wait: the MMAs consumed them)
+            for (int s = 0; s < NS; ++s)
+                if (last[s] != kNone) tc::mbar_wait(&B.full[s], (last[s] / NS) & 1);
         }
     } else if (warp == 6) {
         // ---- TMA producer: epilogue boxes of X ----------------------------------------------
         if (lane == 0) {
             uint32_t ei = 0;
-            for (int64_t tile = first; tile < a.tiles; tile += step)
+            uint32_t last[kMaxStages];  // load index that last armed each box
+            for (int e = 0; e < kMaxStages; ++e) last[e] = kNone;
+            for (int64_t tile = first; tile < a.tiles && !aborted(); tile += step)
                 for (int j = 0; j < NC; ++j, ++ei) {
                     const uint32_t e = ei % NE;
                     wait(&B.eempty[e], ((ei / NE) & 1) ^ 1);
+                    if (aborted()) break;
+                    last[e] = ei;
                     tc::mbar_expect_tx(&B.efull[e], kEBox);
                     tc::tma_load_2d(ering + e * kEBox, &mapX, (NC - 1 - j) * kChunkN,
                                     (int)(tile * kTileM), &B.efull[e]);
                 }
+            for (int e = 0; e < NE; ++e)
+                if (last[e] != kNone) tc::mbar_wait(&B.efull[e], (last[e] / NE) & 1);
         }
     } else if (warp == 1) {
         // ---- MMA issuer ---------------------------------------------------------------------
@@ -328,6 +350,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
             auto mma1 = [&](int kc) {
                 const uint32_t s = it % NS;
                 wait(&B.full[s], (it / NS) & 1);
+                if (aborted()) return;
                 tc::tc_fence_after();
                 const uint32_t sa = tc::smem_u32(ring + s * stage_bytes), sb = sa + bytesX;
 #pragma unroll
@@ -342,6 +365,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                 wait(&B.acc_empty[c], ((ai / kNumAcc) & 1) ^ 1);
                 const uint32_t s = it % NS;
                 wait(&B.full[s], (it / NS) & 1);
+                if (aborted()) return;
                 tc::tc_fence_after();
                 const uint32_t sb = tc::smem_u32(ring + s * stage_bytes);
                 const uint32_t tacc = tz + kTmemAcc + c * kChunkN;
@@ -358,7 +382,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                 for (int kc = 0; kc < KC; ++kc) mma1(kc);
                 tc::mma_commit(&B.z_full);
             }
-            for (int64_t tile = first; tile < a.tiles; tile += step, ++ti) {
+            for (int64_t tile = first; tile < a.tiles && !aborted(); tile += step, ++ti) {
                 const bool next = tile + step < a.tiles;
                 wait(&B.zs_full, ti & 1);  // Z of this tile is in BF16 columns; the FP32 ones are free
                 tc::tc_fence_after();
@@ -369,7 +393,11 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                 if (next) tc::mma_commit(&B.z_full);
                 tc::mma_commit(&B.zs_free);  // GEMM 2 of this tile has read the BF16 Z
             }
-            if (ti > 0) wait(&B.zs_free, (ti - 1) & 1);  // last commit landed before exit
+            // every MMA issued by this thread (and its commits) has completed
+            // before tensor memory is freed, also after a wait was given up
+            if (ti > 0) tc::mbar_wait(&B.zs_free, (ti - 1) & 1);
+            tc::mma_commit(&B.drain);
+            tc::mbar_wait(&B.drain, 0);
         }
     } else {
         // ---- epilogue: warps 2..5, tensor-memory lane quadrant warp % 4 ----------------------
@@ -567,14 +595,14 @@ hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void
     if ((uintptr_t)X % 16 || (uintptr_t)Y % 16 || ldx % 8 || ldy % 8)
         return fail(HH_ERR_UNSUPPORTED,
                     "compact-WY path: X and Y need 16-byte aligned rows (ld a multiple of 8)");
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(wy::wy_panel_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)wy::kSmemBytes);
-        if (e) return cuda_fail(e, "compact-WY shared-memory opt-in");
-        attr = true;
-    }
+    static PerDevice attr;  // the shared-memory opt-in, once per device
+    int unused = 0;
+    cudaError_t ea = per_device(attr, unused, [](int &) {
+        return cudaFuncSetAttribute(wy::wy_panel_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)wy::kSmemBytes);
+    });
+    if (ea) return cuda_fail(ea, "compact-WY shared-memory opt-in");
     const int64_t tiles = (batch + wy::kTileM - 1) / wy::kTileM;
     if (tiles * wy::kTileM > 0x7fffffffLL) return fail(HH_ERR_INVALID_ARG, "batch too large");
     const int grid = (int)std::min<int64_t>(tiles, p->num_sms > 0 ? p->num_sms : 1);
