@@ -1,6 +1,6 @@
 // F32 instantiations of the fused chain kernels.  Configurations are picked by
 // the number of columns n; COVER = G * NG * 4 columns per row group.
-#include "hh_staged.cuh"
+#include "hh_split.cuh"
 
 // Measured (G, NG, RT, RG, B) of the staged configurations for n <= 1024,
 // n <= 2048 and n <= 4096 (overridable at compile time for tuning runs).  The
@@ -28,6 +28,16 @@
 #define HH_N4096_B 2
 #endif
 
+// Column-split cluster kernel for 2048 < n <= 4096 (each CTA of a pair keeps
+// its 2048 columns of every reflector in shared memory): (G, NG, RT, RG, B).
+#ifndef HH_SPLIT_G
+#define HH_SPLIT_G 64
+#define HH_SPLIT_NG 8
+#define HH_SPLIT_RT 4
+#define HH_SPLIT_RG 4
+#define HH_SPLIT_B 2
+#endif
+
 namespace hh {
 
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
@@ -50,6 +60,12 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
         if (n <= 512) return HH_STAGED(32, 4, 4, 4, 2);
         if (n <= 1024) return HH_STAGED(HH_N1024_G, HH_N1024_NG, HH_N1024_RT, HH_N1024_RG, HH_N1024_B);
         if (n <= 2048) return HH_STAGED(HH_N2048_G, HH_N2048_NG, HH_N2048_RT, HH_N2048_RG, HH_N2048_B);
+#ifndef HH_NO_SPLIT
+        if (n > 2048 && n <= 4096 &&
+            h <= split::max_h<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>())
+            return split::launch<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>(
+                mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, d, err, st);
+#endif
         if (n <= 4096) return HH_STAGED(HH_N4096_G, HH_N4096_NG, HH_N4096_RT, HH_N4096_RG, HH_N4096_B);
         return HH_STAGED(512, 4, 2, 1, 2);
 #undef HH_STAGED

@@ -1,0 +1,436 @@
+// Column-split F32 reflector-chain kernel on two-CTA clusters.
+//
+// The arithmetic is the staged kernel's: the chain of §II-A (Eq. (1)-(2)),
+// B consecutive reflectors per round, with the dot products of a round taken
+// against the round's input and the sequential coefficients recovered exactly
+// from the FP64 Gram entries,
+//     z_j = v_j . x,   c_j = tau_j (z_j - sum_{i<j} c_i (v_i . v_j)),
+//     x <- x - sum_j c_j v_j.
+// What changes is where the reflector values come from.  The two CTAs of a
+// cluster split every vector's columns in half, and each keeps its half of all
+// h reflectors resident in shared memory for the whole persistent kernel, so
+// inside the loop no reflector value is read from L2.  The price is one
+// exchange per round: each CTA's dot products cover half the columns, and the
+// halves are added by storing the CTA's partial sums into the peer CTA's
+// receive slot through distributed shared memory (st.async, completing on
+// the peer's mbarrier).  Both CTAs form q_own + q_peer; IEEE addition is
+// commutative, so both halves of a vector see bit-identical coefficients.
+//
+// Vectors go from HBM straight into registers (16-byte loads, each warp
+// reading 512-byte runs); while a tile is computed the bulk-copy engine
+// prefetches the row group's next tile into L2, and results leave with
+// streaming stores.  Each vector is read once and written once.
+//
+// Layout.  A CTA is RG row groups of G threads; thread t of a group owns
+// granules t + G*i (i < NG) of 4 floats, within this CTA's half, of each of
+// the group's RT rows.  Row group rg of both CTAs of cluster c walks the same
+// tiles of RT rows, c*RG + rg + k*(clusters*RG).
+//
+// Waits are bounded (about a second of clock cycles).  On expiry the thread
+// records HH_ERR_TIMEOUT in *err and stops waiting; control flow stays
+// uniform (every thread runs every round), so no barrier is left unmatched,
+// and the kernel ends with a cluster barrier so that no CTA leaves while its
+// peer may still store into it.
+#pragma once
+
+#include "hh_staged.cuh"
+
+namespace hh {
+namespace split {
+
+using staged::bulk_g2s;
+using staged::fence_proxy_async;
+using staged::kGramBand;
+using staged::kWaitCycles;
+using staged::mbar_expect_tx;
+using staged::mbar_init;
+using staged::smem_u32;
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Address of the same shared-memory variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+// Store one float into a peer CTA's shared memory; the store completes 4 bytes
+// of the transaction count of the peer's mbarrier at `bar`.
+__device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+                     addr),
+                 "r"(__float_as_uint(v)), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbarrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n\t"
+        "barrier.cluster.wait.acquire.aligned;" ::
+            : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// Phase-parity wait with acquire at cluster scope (the phase is completed by
+// a peer CTA's stores), bounded by about a second of clock cycles.
+__device__ __forceinline__ bool try_wait_cluster(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool wait_cluster_bounded(uint64_t *bar, uint32_t parity) {
+    if (try_wait_cluster(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!try_wait_cluster(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+template <int G, int NG, int RT, int RG, int B>
+struct XCfg {
+    static constexpr int E = NG * 4;      // floats of one row held by a thread
+    static constexpr int E2 = E / 2;      // float2 pairs
+    static constexpr int NW = G / 32;     // warps per row group
+    static constexpr int THREADS = G * RG;
+    static constexpr int HALF = G * E;    // columns owned by one CTA of the pair
+    static constexpr int NV = B * RT;     // dot products reduced together
+    static constexpr int L = 32 / NV;     // lanes holding one value after the warp reduction
+    static_assert(G % 32 == 0, "G must be a multiple of 32");
+    static_assert(NV <= 32 && (NV & (NV - 1)) == 0, "B*RT must be a power of two <= 32");
+    static_assert(B >= 1 && B <= kGramBand, "block larger than the stored Gram band");
+};
+
+// Scale the held columns (this CTA's half, starting at column c0) by s.
+template <int G, int NG, int RT, int RG, int B>
+__device__ __forceinline__ void scale_half(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2],
+                                           const float *__restrict__ s, int c0, int t) {
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        float4 q = __ldg(reinterpret_cast<const float4 *>(s + c0) + (t + G * i));
+        const float2 lo = make_float2(q.x, q.y), hi = make_float2(q.z, q.w);
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            x[r][2 * i] = __fmul2_rn(x[r][2 * i], lo);
+            x[r][2 * i + 1] = __fmul2_rn(x[r][2 * i + 1], hi);
+        }
+    }
+}
+
+// Per-row-group exchange state: the round counter selects the receive buffer
+// (round & 1) and the phase parity of its mbarrier ((round >> 1) & 1).
+struct Exchange {
+    uint32_t round;
+    uint32_t peer_slot;  // the peer CTA's receive slots of this row group (shared::cluster)
+    uint32_t peer_bar;   // the peer CTA's receive mbarriers of this row group
+    bool waiting;        // false once a wait of this thread expired
+};
+
+// Apply h reflectors, ascending (k = 0..h-1) or descending, to the RT rows in
+// x, B per round.  vs holds this CTA's half of every reflector (row k at
+// vs + k*HALF).
+template <int G, int NG, int RT, int RG, int B>
+__device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2], bool asc, int h,
+                                      const float *vs, const float *__restrict__ tau,
+                                      const float *__restrict__ gram, int t, int lane, int warp,
+                                      int rg, float *red, int &buf, float *slot, uint64_t *bars,
+                                      Exchange &xc, int *err) {
+    using C = XCfg<G, NG, RT, RG, B>;
+    constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L, HALF = C::HALF;
+    auto load_u = [&](int s0, int j, float2(&dst)[E2]) {
+        const bool ok = s0 + j < h;
+        const int k = asc ? s0 + j : h - 1 - s0 - j;
+        const float4 *row = reinterpret_cast<const float4 *>(vs + (size_t)(ok ? k : 0) * HALF);
+#pragma unroll
+        for (int i = 0; i < NG; ++i) {
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) q = row[t + G * i];
+            dst[2 * i] = make_float2(q.x, q.y);
+            dst[2 * i + 1] = make_float2(q.z, q.w);
+        }
+    };
+    for (int s = 0; s < h; s += B) {
+        const int nb = h - s < B ? h - s : B;
+        // tau and the Gram entries of the round (uniform scalars through L1),
+        // read before the reduction so their latency is not exposed after it
+        float tk[B], gv[B][B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int kj = asc ? s + j : h - 1 - s - j;
+            tk[j] = j < nb ? __ldg(tau + kj) : 0.f;
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                const int ki = asc ? s + i : h - 1 - s - i;
+                gv[j][i] = (i > j && i < nb)
+                               ? __ldg(gram + (size_t)(asc ? kj : ki) * kGramBand + (i - j))
+                               : 0.f;
+            }
+        }
+        float p[NV];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            float2 u[E2];
+            load_u(s, j, u);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < E2; ++e) a = __ffma2_rn(x[r][e], u[e], a);
+                p[j * RT + r] = a.x + a.y;
+            }
+        }
+        float q = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
+        const int idx = lane / L, sub = lane & (L - 1);
+        if constexpr (NW > 1) {
+            if (sub == 0) red[fused::red_index<RG, NV, NW>(buf, rg, idx, warp)] = q;
+            if constexpr (RG > 1)
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "n"(G) : "memory");
+            else
+                __syncthreads();
+            float w = 0.f;
+#pragma unroll
+            for (int ww = sub; ww < NW; ww += L) w += red[fused::red_index<RG, NV, NW>(buf, rg, idx, ww)];
+#pragma unroll
+            for (int off = L / 2; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+            q = w;
+            buf ^= 1;
+        }
+        // q: this CTA's half of value idx, held by the L lanes of idx.  Warp 0
+        // sends it to the peer; every warp then waits for the peer's half.
+        const uint32_t b = xc.round & 1u, par = (xc.round >> 1) & 1u;
+        if (warp == 0) {
+            if (sub == 0)
+                st_async_f32(xc.peer_slot + (b * NV + idx) * 4u, q, xc.peer_bar + b * 8u);
+            if (lane == 0) mbar_expect_tx(bars + b, NV * 4u);
+        }
+        if (xc.waiting && !wait_cluster_bounded(bars + b, par)) {
+            atomicExch(err, (int)HH_ERR_TIMEOUT);
+            xc.waiting = false;
+        }
+        const float zz = q + slot[b * NV + idx];
+        ++xc.round;
+        float z[NV];
+#pragma unroll
+        for (int qq = 0; qq < NV; ++qq) z[qq] = __shfl_sync(0xffffffffu, zz, qq * L);
+        // coefficients in the order the reflectors act, stored negated
+        float c[B][RT];
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+#pragma unroll
+            for (int r = 0; r < RT; ++r) c[j][r] = z[j * RT + r];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+#pragma unroll
+            for (int r = 0; r < RT; ++r) c[j][r] *= -tk[j];
+#pragma unroll
+            for (int i = j + 1; i < B; ++i) {
+#pragma unroll
+                for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], gv[j][i], c[i][r]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            float2 u[E2];
+            load_u(s, j, u);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const float2 cc = make_float2(c[j][r], c[j][r]);
+#pragma unroll
+                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(u[e], cc, x[r][e]);
+            }
+        }
+    }
+}
+
+// Requirements (checked by the launcher): HALF < n <= 2*HALF, n % 4 == 0, X and
+// Y rows and bases 16-byte aligned, V rows zero padded to ldv >= 2*HALF,
+// ldv % 4 == 0, h*HALF floats of dynamic shared memory.  Launched as clusters
+// of two CTAs (cluster rank = the half of the columns a CTA owns).
+template <int MODE, int G, int NG, int RT, int RG, int B>
+__global__ void __launch_bounds__(G *RG, 1)
+split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t batch, int n,
+                   const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv, int h,
+                   const float *__restrict__ gram, const float *__restrict__ sign,
+                   const float *__restrict__ d, int *__restrict__ err) {
+    using C = XCfg<G, NG, RT, RG, B>;
+    constexpr int E2 = C::E2, NV = C::NV, HALF = C::HALF;
+    extern __shared__ __align__(128) float vs[];  // h x HALF: this CTA's half of every reflector
+    __shared__ __align__(8) uint64_t vbar;
+    __shared__ __align__(8) uint64_t rbar[RG][2];    // the peer's halves arrive on these
+    __shared__ __align__(16) float rslot[RG][2][NV];  // ... into these
+    __shared__ __align__(16) float red[2 * RG * NV * C::NW];
+
+    const int tid = threadIdx.x;
+    const int rg = tid / G;
+    const int t = tid - rg * G;
+    const int warp = t >> 5, lane = t & 31;
+    const uint32_t rank = cluster_rank();
+    const int c0 = (int)rank * HALF;  // first column of this CTA's half
+    const int64_t cid = cluster_id(), ncl = cluster_count();
+    const int ncols = n - c0 < HALF ? n - c0 : HALF;  // columns of this half inside n
+
+    if (tid == 0) {
+        mbar_init(&vbar, 1);
+        for (int g = 0; g < RG; ++g) {
+            mbar_init(&rbar[g][0], 1);
+            mbar_init(&rbar[g][1], 1);
+        }
+        fence_mbarrier_init();
+        fence_proxy_async();
+        if (h > 0) {
+            mbar_expect_tx(&vbar, (uint32_t)h * HALF * 4u);
+            for (int k = 0; k < h; ++k)
+                bulk_g2s(vs + (size_t)k * HALF, V + (size_t)k * ldv + c0, HALF * 4u, &vbar);
+        }
+    }
+    // every mbarrier of the cluster is initialised before any peer stores into it
+    cluster_sync();
+    Exchange xc;
+    xc.round = 0;
+    xc.peer_slot = peer_addr(smem_u32(&rslot[rg][0][0]), rank ^ 1u);
+    xc.peer_bar = peer_addr(smem_u32(&rbar[rg][0]), rank ^ 1u);
+    xc.waiting = true;
+    if (h > 0 && !wait_cluster_bounded(&vbar, 0)) {
+        atomicExch(err, (int)HH_ERR_TIMEOUT);
+        wait_cluster_bounded(&vbar, 0);  // give the copy in flight one more chance
+        xc.waiting = false;
+    }
+
+    const int64_t rtiles = (batch + RT - 1) / RT;
+    int buf = 0;
+    for (int64_t tl = cid * RG + rg; tl < rtiles; tl += ncl * RG) {
+        const int64_t r0 = tl * RT;
+        // the group's next tile into L2 while this one is computed
+        if (t == 0) {
+            const int64_t nr0 = (tl + ncl * RG) * RT;
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+                if (nr0 + r < batch) prefetch_l2(X + (nr0 + r) * ldx + c0, (uint32_t)ncols * 4u);
+        }
+        float2 x[RT][E2];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const bool valid = r0 + r < batch;
+            const float *xr = X + (r0 + r) * ldx + c0;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const int col = (t + G * i) * 4;
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (valid && col < ncols) q = __ldcs(reinterpret_cast<const float4 *>(xr + col));
+                x[r][2 * i] = make_float2(q.x, q.y);
+                x[r][2 * i + 1] = make_float2(q.z, q.w);
+            }
+        }
+        if (MODE != HH_MODE_W && sign) scale_half<G, NG, RT, RG, B>(x, sign, c0, t);
+        // W: k = h..1; W^T: k = 1..h; S: k = 1..h, scale by d, k = h..1
+        for (int half = 0; half < (MODE == HH_MODE_SYM ? 2 : 1); ++half) {
+            if (half == 1) scale_half<G, NG, RT, RG, B>(x, d, c0, t);
+            const bool asc = MODE != HH_MODE_W && half == 0;
+            chain<G, NG, RT, RG, B>(x, asc, h, vs, tau, gram, t, lane, warp, rg, red, buf,
+                                    &rslot[rg][0][0], &rbar[rg][0], xc, err);
+        }
+        if (MODE != HH_MODE_WT && sign) scale_half<G, NG, RT, RG, B>(x, sign, c0, t);
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            if (r0 + r >= batch) continue;
+            float *yr = Y + (r0 + r) * ldy + c0;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const int col = (t + G * i) * 4;
+                if (col < ncols)
+                    __stcs(reinterpret_cast<float4 *>(yr + col),
+                           make_float4(x[r][2 * i].x, x[r][2 * i].y, x[r][2 * i + 1].x,
+                                       x[r][2 * i + 1].y));
+            }
+        }
+    }
+    // no CTA leaves while its peer may still store into its receive slots
+    __syncthreads();
+    cluster_sync();
+}
+
+// Largest dynamic shared memory a launch may request (h*HALF floats).
+constexpr size_t kMaxSmem = 200 * 1024;
+
+template <int G, int NG, int RT, int RG, int B>
+constexpr int max_h() {
+    return (int)(kMaxSmem / (XCfg<G, NG, RT, RG, B>::HALF * sizeof(float)));
+}
+
+template <int G, int NG, int RT, int RG, int B>
+cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
+                   int64_t batch, int n, const float *V, const float *tau, int64_t ldv, int h,
+                   const float *gram, const float *sign, const float *d, int *err,
+                   cudaStream_t st) {
+    using C = XCfg<G, NG, RT, RG, B>;
+    if (n <= C::HALF || n > 2 * C::HALF || n % 4 || ldv < 2 * C::HALF || ldv % 4 ||
+        h > max_h<G, NG, RT, RG, B>())
+        return cudaErrorInvalidValue;
+    const size_t smem = h > 0 ? (size_t)h * C::HALF * sizeof(float) : 16;
+    // per kernel (one per mode) and device: the shared-memory opt-in at the
+    // largest request, and the co-resident clusters measured with it
+    static PerDevice state[3];
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(C::THREADS);
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 1;
+        cudaError_t e = per_device(state[mode], ncl, [&](int &v) -> cudaError_t {
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)kMaxSmem);
+            if (e2 != cudaSuccess) return e2;
+            cudaLaunchConfig_t q = cfg;
+            q.gridDim = dim3(2);
+            q.dynamicSmemBytes = kMaxSmem;
+            int nc = 0;
+            e2 = cudaOccupancyMaxActiveClusters(&nc, kern, &q);
+            if (e2 != cudaSuccess) return e2;
+            v = nc > 0 ? nc : 1;
+            return cudaSuccess;
+        });
+        if (e != cudaSuccess) return e;
+        const int64_t groups = ((batch + RT - 1) / RT + RG - 1) / RG;  // row-group tiles / RG
+        const int grid_cl = (int)(groups < ncl ? groups : ncl);
+        cfg.gridDim = dim3(2 * grid_cl);
+        cfg.dynamicSmemBytes = smem;
+        return cudaLaunchKernelEx(&cfg, kern, X, ldx, Y, ldy, batch, n, V, tau, ldv, h, gram,
+                                  sign, d, err);
+    };
+    switch (mode) {
+        case HH_MODE_W: return run(split_chain_kernel<HH_MODE_W, G, NG, RT, RG, B>);
+        case HH_MODE_WT: return run(split_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B>);
+        default: return run(split_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B>);
+    }
+}
+
+}  // namespace split
+}  // namespace hh
