@@ -35,7 +35,7 @@
 #define HH_SPLIT_NG 8
 #define HH_SPLIT_RT 4
 #define HH_SPLIT_RG 4
-#define HH_SPLIT_B 2
+#define HH_SPLIT_B 4
 #endif
 
 namespace hh {

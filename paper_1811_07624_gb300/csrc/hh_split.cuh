@@ -10,11 +10,15 @@
 // cluster split every vector's columns in half, and each keeps its half of all
 // h reflectors resident in shared memory for the whole persistent kernel, so
 // inside the loop no reflector value is read from L2.  The price is one
-// exchange per round: each CTA's dot products cover half the columns, and the
-// halves are added by storing the CTA's partial sums into the peer CTA's
-// receive slot through distributed shared memory (st.async, completing on
-// the peer's mbarrier).  Both CTAs form q_own + q_peer; IEEE addition is
-// commutative, so both halves of a vector see bit-identical coefficients.
+// exchange per round: each warp's dot products cover its share of one half of
+// the columns.  After a shuffle reduction inside the warp, every warp stores
+// its partial sums into a receive slot of its own CTA (shared store, then an
+// mbarrier arrival) and into the same slot of the peer CTA through
+// distributed shared memory (st.async, completing bytes on the peer's
+// mbarrier).  One barrier phase per round thus gathers all partial sums of
+// both CTAs, with no named barrier between the warps, and both CTAs add them
+// in the same fixed order, so both halves of a vector see bit-identical
+// coefficients.
 //
 // Vectors go from HBM straight into registers (16-byte loads, each warp
 // reading 512-byte runs); while a tile is computed the bulk-copy engine
@@ -73,6 +77,16 @@ __device__ __forceinline__ void st_async_f32(uint32_t addr, float v, uint32_t ba
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
                      addr),
                  "r"(__float_as_uint(v)), "r"(bar)
+                 : "memory");
+}
+// Arrive on a local mbarrier (release at CTA scope), optionally raising the
+// phase's expected transaction bytes first.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
                  : "memory");
 }
 __device__ __forceinline__ void fence_mbarrier_init() {
@@ -143,6 +157,7 @@ __device__ __forceinline__ void scale_half(float2 (&x)[RT][XCfg<G, NG, RT, RG, B
 // (round & 1) and the phase parity of its mbarrier ((round >> 1) & 1).
 struct Exchange {
     uint32_t round;
+    uint32_t rank;       // this CTA's rank in the cluster
     uint32_t peer_slot;  // the peer CTA's receive slots of this row group (shared::cluster)
     uint32_t peer_bar;   // the peer CTA's receive mbarriers of this row group
     bool waiting;        // false once a wait of this thread expired
@@ -155,10 +170,10 @@ template <int G, int NG, int RT, int RG, int B>
 __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2], bool asc, int h,
                                       const float *vs, const float *__restrict__ tau,
                                       const float *__restrict__ gram, int t, int lane, int warp,
-                                      int rg, float *red, int &buf, float *slot, uint64_t *bars,
-                                      Exchange &xc, int *err) {
+                                      float *slot, uint64_t *bars, Exchange &xc, int *err) {
     using C = XCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L, HALF = C::HALF;
+    (void)NW;
     auto load_u = [&](int s0, int j, float2(&dst)[E2]) {
         const bool ok = s0 + j < h;
         const int k = asc ? s0 + j : h - 1 - s0 - j;
@@ -203,33 +218,34 @@ __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2
         }
         float q = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
         const int idx = lane / L, sub = lane & (L - 1);
-        if constexpr (NW > 1) {
-            if (sub == 0) red[fused::red_index<RG, NV, NW>(buf, rg, idx, warp)] = q;
-            if constexpr (RG > 1)
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "n"(G) : "memory");
-            else
-                __syncthreads();
-            float w = 0.f;
-#pragma unroll
-            for (int ww = sub; ww < NW; ww += L) w += red[fused::red_index<RG, NV, NW>(buf, rg, idx, ww)];
-#pragma unroll
-            for (int off = L / 2; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
-            q = w;
-            buf ^= 1;
-        }
-        // q: this CTA's half of value idx, held by the L lanes of idx.  Warp 0
-        // sends it to the peer; every warp then waits for the peer's half.
+        // q: this warp's part of value idx, held by the L lanes of idx.  Every
+        // warp posts its part into slot [b][rank][warp][idx] of both CTAs: its
+        // own with a shared store and an arrival, the peer's with st.async,
+        // which completes bytes on the peer's mbarrier.  Once a CTA's barrier
+        // phase completes it holds all 2*NW parts, and both CTAs add them in
+        // the same fixed order.
         const uint32_t b = xc.round & 1u, par = (xc.round >> 1) & 1u;
-        if (warp == 0) {
-            if (sub == 0)
-                st_async_f32(xc.peer_slot + (b * NV + idx) * 4u, q, xc.peer_bar + b * 8u);
-            if (lane == 0) mbar_expect_tx(bars + b, NV * 4u);
+        if (sub == 0) {
+            const uint32_t off = ((b * 2u + xc.rank) * NW + warp) * NV + idx;
+            slot[off] = q;
+            st_async_f32(xc.peer_slot + off * 4u, q, xc.peer_bar + b * 8u);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (warp == 0)
+                mbar_arrive_expect_tx(bars + b, NW * NV * 4u);  // + the peer's parts
+            else
+                mbar_arrive(bars + b);
         }
         if (xc.waiting && !wait_cluster_bounded(bars + b, par)) {
             atomicExch(err, (int)HH_ERR_TIMEOUT);
             xc.waiting = false;
         }
-        const float zz = q + slot[b * NV + idx];
+        float zz = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int w = 0; w < NW; ++w) zz += slot[((b * 2u + c) * NW + w) * NV + idx];
         ++xc.round;
         float z[NV];
 #pragma unroll
@@ -278,9 +294,10 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
     constexpr int E2 = C::E2, NV = C::NV, HALF = C::HALF;
     extern __shared__ __align__(128) float vs[];  // h x HALF: this CTA's half of every reflector
     __shared__ __align__(8) uint64_t vbar;
-    __shared__ __align__(8) uint64_t rbar[RG][2];    // the peer's halves arrive on these
-    __shared__ __align__(16) float rslot[RG][2][NV];  // ... into these
-    __shared__ __align__(16) float red[2 * RG * NV * C::NW];
+    // per row group, two buffers of 2 CTAs x NW warps x NV partial dot products,
+    // each completed on its own mbarrier (NW local arrivals + the peer's bytes)
+    __shared__ __align__(8) uint64_t rbar[RG][2];
+    __shared__ __align__(16) float rslot[RG][2 * 2 * C::NW * NV];
 
     const int tid = threadIdx.x;
     const int rg = tid / G;
@@ -294,8 +311,8 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
     if (tid == 0) {
         mbar_init(&vbar, 1);
         for (int g = 0; g < RG; ++g) {
-            mbar_init(&rbar[g][0], 1);
-            mbar_init(&rbar[g][1], 1);
+            mbar_init(&rbar[g][0], C::NW);
+            mbar_init(&rbar[g][1], C::NW);
         }
         fence_mbarrier_init();
         fence_proxy_async();
@@ -309,7 +326,8 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
     cluster_sync();
     Exchange xc;
     xc.round = 0;
-    xc.peer_slot = peer_addr(smem_u32(&rslot[rg][0][0]), rank ^ 1u);
+    xc.rank = rank;
+    xc.peer_slot = peer_addr(smem_u32(&rslot[rg][0]), rank ^ 1u);
     xc.peer_bar = peer_addr(smem_u32(&rbar[rg][0]), rank ^ 1u);
     xc.waiting = true;
     if (h > 0 && !wait_cluster_bounded(&vbar, 0)) {
@@ -319,7 +337,6 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
     }
 
     const int64_t rtiles = (batch + RT - 1) / RT;
-    int buf = 0;
     for (int64_t tl = cid * RG + rg; tl < rtiles; tl += ncl * RG) {
         const int64_t r0 = tl * RT;
         // the group's next tile into L2 while this one is computed
@@ -348,8 +365,8 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
         for (int half = 0; half < (MODE == HH_MODE_SYM ? 2 : 1); ++half) {
             if (half == 1) scale_half<G, NG, RT, RG, B>(x, d, c0, t);
             const bool asc = MODE != HH_MODE_W && half == 0;
-            chain<G, NG, RT, RG, B>(x, asc, h, vs, tau, gram, t, lane, warp, rg, red, buf,
-                                    &rslot[rg][0][0], &rbar[rg][0], xc, err);
+            chain<G, NG, RT, RG, B>(x, asc, h, vs, tau, gram, t, lane, warp, &rslot[rg][0],
+                                    &rbar[rg][0], xc, err);
         }
         if (MODE != HH_MODE_WT && sign) scale_half<G, NG, RT, RG, B>(x, sign, c0, t);
 #pragma unroll
