@@ -16,6 +16,8 @@ Recipes (each a numpy ``default_rng(seed)``, PCG64):
 * vectors ``X``: ``B x n``, i.i.d. N(0, 1);
 * random orthonormal matrix: Gaussian matrix, then QR, keep Q (the recipe the
   paper states in §II-D);
+* random symmetric targets for the factorization of §III: indefinite
+  (X + X^T)/2 and positive semidefinite X X^T, X i.i.d. N(0, 1);
 * a symmetric target with decaying spectrum and a Gaussian-mixture metric
   learning set (the differentiation workloads).
 
@@ -92,6 +94,20 @@ def decaying_symmetric(n: int, seed: int = 0, power: float = 1.5):
     q = random_orthonormal(n, seed)
     lam = np.arange(1, n + 1, dtype=np.float64) ** (-power)
     return (q * lam) @ q.T, q, lam
+
+
+def random_symmetric(n: int, seed: int = 0) -> np.ndarray:
+    """Indefinite symmetric S = (X + X^T) / 2 with X i.i.d. N(0, 1) (§III-D,
+    the random symmetric matrices of Result 4 and of the §IV experiments)."""
+    x = rng(seed + 5).standard_normal((n, n))
+    return 0.5 * (x + x.T)
+
+
+def random_wishart(n: int, seed: int = 0) -> np.ndarray:
+    """Positive semidefinite S = X X^T with X i.i.d. N(0, 1) (the Wishart
+    matrices of the remark after Result 4)."""
+    x = rng(seed + 6).standard_normal((n, n))
+    return x @ x.T
 
 
 def gaussian_mixture(n_points: int, n: int = 256, classes: int = 10, seed: int = 0,
