@@ -285,7 +285,8 @@ def shf(S, h, K=10, spectrum_update_=False, inner=20, inner_tol=1e-12, tol=1e-7,
     reflector vectors; the Result-4 start of §III-D passes them).  Returns a
     dict with U (h x n, unit or zero rows), s_bar, d, the objective after each
     outer iteration ("history", index 0 = after step 2) and, with trace=True,
-    the per-reflector C values and objective after every reflector update.
+    the per-reflector C values and objective after every reflector update,
+    with the state (U before and after, d, s_bar) each update started from.
     """
     S = np.asarray(S, dtype=np.float64)
     n = S.shape[0]
@@ -309,6 +310,7 @@ def shf(S, h, K=10, spectrum_update_=False, inner=20, inner_tol=1e-12, tol=1e-7,
         for k in range(h):
             A = A_mat(S, U, d, k)
             B = B_mat(U, s_bar, k)
+            before = U.copy()
             if np.any(U[k]):
                 u, cs = descend(U[k], A, B, inner=inner, inner_tol=inner_tol)
                 U[k] = u
@@ -320,7 +322,9 @@ def shf(S, h, K=10, spectrum_update_=False, inner=20, inner_tol=1e-12, tol=1e-7,
                     U[k] = u
                 cs = [0.0, min(cs[-1], 0.0)]
             if trace:
-                steps.append({"k": k, "C": cs, "objective": objective(S, U, s_bar, d)})
+                steps.append({"k": k, "C": cs, "objective": objective(S, U, s_bar, d),
+                              "U_before": before, "U": U.copy(), "d": d.copy(),
+                              "s_bar": s_bar.copy()})
         d = optimal_sign(S, B_mat(U, s_bar, -1))
         if spectrum_update_:
             s_bar = spectrum_update(S, U, d)
