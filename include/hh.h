@@ -126,6 +126,21 @@ hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype,
                        hh_path *path);
 
 /*
+ * Zero prefixes of the reflectors (§II-D, the remark after Result 3: the
+ * reflectors of a partial QR factorization have k - 1 leading zeros, so H_k
+ * costs 4(n - k + 1) operations instead of 4n).  At create, and at every
+ * hh_update, the plan records the first non-zero column of each v_k; when the
+ * zero prefixes hold at least 1/16 of U's entries, F32 applies with n <= 8192
+ * on 16-byte aligned rows skip, per round of reflectors, the column blocks
+ * that lie before every reflector's first non-zero (exact: the skipped terms
+ * are zeros).  mode 1 turns the skipping on, 0 off, -1 back to that automatic
+ * choice, -2 leaves it as it is; *enabled (may be NULL) receives the setting
+ * now in force.  Other modes: HH_ERR_INVALID_ARG.  Host-side
+ * only, no device work; F64 and BF16 plans accept the call and never skip.
+ */
+hh_status hh_plan_skip_prefix(hh_plan_t plan, int mode, int *enabled);
+
+/*
  * Y = sigma .* (W X) row by row (§II-A, Eq. (1)).  X: batch x n, row stride
  * ldx; Y: batch x n, row stride ldy.  batch == 0 is a no-op.
  */

@@ -52,6 +52,7 @@ SIGNATURES = {
     "hh_destroy": [vp],
     "hh_sync": [vp, vp],
     "hh_update": [vp, vp, i64, vp, vp],
+    "hh_plan_skip_prefix": [vp, ip, ctypes.POINTER(ip)],
     "hh_plan_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(ip),
                      ctypes.POINTER(ip)],
     "hh_apply": [vp, vp, i64, vp, i64, i64, vp],

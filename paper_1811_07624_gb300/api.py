@@ -131,6 +131,15 @@ class Plan:
     def handle(self) -> ctypes.c_void_p:
         return self._h
 
+    def skip_prefix(self, mode: int | None = None) -> bool:
+        """Skipping of the reflectors' zero prefixes (§II-D): True/1 on, False/0
+        off, -1 back to the automatic choice made at create; None only reads.
+        Returns the setting in force."""
+        out = ctypes.c_int()
+        _lib.call("hh_plan_skip_prefix", self._h, -2 if mode is None else int(mode),
+                  ctypes.byref(out))
+        return bool(out.value)
+
     # -- forward ------------------------------------------------------------------
     def _apply(self, fn: str, X: torch.Tensor, out: torch.Tensor | None, stream) -> torch.Tensor:
         xp, ldx = _rows(X, "X", self.n, self.dtype)

@@ -3,6 +3,7 @@
 #include <stdio.h>
 
 #include <new>
+#include <vector>
 
 #include "hh_internal.cuh"
 
@@ -54,6 +55,7 @@ static void free_plan(Plan *p) {
     cudaFree(p->vnorm);
     cudaFree(p->err);
     cudaFree(p->upd);
+    cudaFree(p->start);
     delete p;
 }
 
@@ -186,6 +188,7 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
         (e = dev_malloc(&p->tau_t, es * (size_t)(h > 0 ? h : 1))) ||
         (e = dev_malloc(&p->gram, es * 16 * (size_t)(h > 0 ? h : 1))) ||
         (e = dev_malloc(&p->vnorm, sizeof(double) * (size_t)(h > 0 ? h : 1))) ||
+        (e = dev_malloc(&p->start, sizeof(int) * (size_t)(h > 0 ? h : 1))) ||
         (d && (e = dev_malloc(&p->d, es * (size_t)p->ldv))) ||
         (sign && (e = dev_malloc(&p->sign, es * (size_t)p->ldv))) ||
         (e = dev_malloc(&p->err, sizeof(int))) || (e = dev_malloc(&p->upd, sizeof(int))) ||
@@ -218,6 +221,20 @@ hh_status hh_create_ex(hh_plan_t *out, int64_t n, int64_t h, const void *U, int6
             goto done;
         }
         if (path == HH_PATH_WY) wy_release_workspace(p);
+        if (path == HH_PATH_FUSED && h > 0 && !(hflag & 1)) {
+            // zero prefixes (e.g. the reflectors of a partial QR factorization):
+            // worth skipping when they hold at least 1/16 of U's entries
+            std::vector<int> hs((size_t)h);
+            if ((e = cudaMemcpy(hs.data(), p->start, sizeof(int) * (size_t)h,
+                                cudaMemcpyDeviceToHost))) {
+                st = cuda_fail(e, "plan preparation");
+                goto done;
+            }
+            double zeros = 0;
+            for (int v : hs) zeros += v;
+            p->skip_auto = zeros * 16.0 >= (double)n * (double)h;
+            p->skip_prefix = p->skip_auto;
+        }
         if (hflag & 1) st = fail(HH_ERR_NONFINITE, "U holds a NaN or Inf");
         else if (hflag & 2) st = fail(HH_ERR_NONFINITE, "d holds a NaN or Inf");
         else if (hflag & 4) st = fail(HH_ERR_INVALID_ARG, "sign holds a value other than +1/-1");
@@ -291,6 +308,17 @@ hh_status hh_plan_info(hh_plan_t plan, int64_t *n, int64_t *h, hh_dtype *dtype, 
     if (h) *h = p->h;
     if (dtype) *dtype = p->dtype;
     if (path) *path = p->path;
+    return HH_OK;
+}
+
+hh_status hh_plan_skip_prefix(hh_plan_t plan, int mode, int *enabled) {
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p) return fail(HH_ERR_INVALID_ARG, "plan is NULL");
+    if (mode < -2 || mode > 1)
+        return fail(HH_ERR_INVALID_ARG, "mode %d (expected -2, -1, 0 or 1)", mode);
+    if (mode != -2 && p->path == HH_PATH_FUSED && p->dtype == HH_F32 && p->h > 0)
+        p->skip_prefix = mode == -1 ? p->skip_auto : mode == 1;
+    if (enabled) *enabled = p->skip_prefix ? 1 : 0;
     return HH_OK;
 }
 

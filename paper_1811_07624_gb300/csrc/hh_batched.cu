@@ -10,14 +10,23 @@
 // engine while the current tile is computed, as in the single-transform staged
 // kernel.
 //
-// Tile shapes.  One kernel holds several (G, NG, RT) layouts of 256 threads:
-// RG = 256 / G row groups of G threads, each thread RT rows x NG granules of 4
-// floats, COVER = G * NG * 4 columns.  A tile picks its transform's shape at
-// run time; a warp whose granule i lies past n skips it (a warp-uniform test),
-// so a transform of n columns costs n, not COVER, columns of arithmetic.
-// Shapes are chosen per (n, h) by the autotuner (hh_tune), which times every
-// shape that covers n on synthetic data and keeps the fastest; untuned
-// shapes fall back to the nearest tuned h for that n, then to a fixed rule.
+// Tile shapes.  One kernel holds several (G, NG, RT, B) layouts of 256
+// threads: RG = 256 / G row groups of G threads, each thread RT rows x NG
+// granules of 4 floats (64 or 128 floats of vector state), COVER = G * NG * 4
+// columns, B reflectors per reduction round.  The arithmetic is the
+// single-transform kernel's chain (staged::chain, the Gram-corrected blocked
+// rounds), instantiated per shape with its partial-cover option: a warp whose
+// granule i lies past n neither reads nor computes it (a warp-uniform test),
+// so a transform of n columns costs n, not COVER, columns of arithmetic.  The
+// kernel runs one CTA of 256 threads per SM with up to 255 registers per
+// thread.  Shapes are chosen per (n, h) by the autotuner (hh_tune), which
+// times every shape that covers n on synthetic data and keeps the fastest;
+// untuned shapes fall back to the nearest tuned h for that n, then to a fixed
+// rule.
+//
+// Streams.  A batch's work counter and task table are shared by its launches;
+// a launch on a stream other than the previous launch's first waits for that
+// launch (an event), so calls on different streams never overlap on them.
 #include <math.h>
 #include <stdio.h>
 
@@ -33,23 +42,24 @@ namespace hh {
 namespace batched {
 
 constexpr int kThreads = 256;
-constexpr int kB = 2;                    // reflectors per reduction round
-constexpr int kNumShapes = 7;
-constexpr int kStageBytes = 64 * 1024;   // ROWS * COVER * 4 for every shape
-constexpr int kRedFloats = 256;          // 2 * RG * (kB * RT) * NW, largest shape
+constexpr int kNumShapes = 10;
+constexpr int kStageBytes = 128 * 1024;  // >= ROWS * COVER * 4 for every shape
+constexpr int kRedFloats = 512;          // >= 2 * RG * (B * RT) * NW for every shape
 
 struct ShapeInfo {
-    int G, NG, RT;
+    int G, NG, RT, B;
 };
-// Every shape keeps RT * NG * 4 = 64 floats of vector state per thread.
 static const ShapeInfo kShape[kNumShapes] = {
-    {32, 2, 8},   // 0: COVER  256, 64 rows per tile
-    {32, 4, 4},   // 1: COVER  512, 32 rows
-    {32, 8, 2},   // 2: COVER 1024, 16 rows
-    {64, 4, 4},   // 3: COVER 1024, 16 rows
-    {64, 8, 2},   // 4: COVER 2048,  8 rows
-    {128, 4, 4},  // 5: COVER 2048,  8 rows
-    {256, 4, 4},  // 6: COVER 4096,  4 rows
+    {32, 1, 16, 2},   // 0: COVER  128, 128 rows per tile,  64 floats per thread
+    {32, 2, 16, 2},   // 1: COVER  256, 128 rows, 128 floats
+    {32, 4, 8, 2},    // 2: COVER  512,  64 rows, 128 floats
+    {32, 8, 4, 2},    // 3: COVER 1024,  32 rows, 128 floats
+    {32, 8, 4, 4},    // 4: COVER 1024,  32 rows, 128 floats, 4 reflectors per round
+    {64, 4, 4, 4},    // 5: COVER 1024,  16 rows,  64 floats, 4 reflectors per round
+    {64, 8, 4, 2},    // 6: COVER 2048,  16 rows, 128 floats
+    {128, 4, 4, 4},   // 7: COVER 2048,   8 rows,  64 floats, 4 reflectors per round
+    {128, 8, 4, 2},   // 8: COVER 4096,   8 rows, 128 floats
+    {32, 4, 8, 4},    // 9: COVER  512,  64 rows, 128 floats, 4 reflectors per round
 };
 inline int shape_cover(int s) { return kShape[s].G * kShape[s].NG * 4; }
 inline int shape_rows(int s) { return kShape[s].RT * (kThreads / kShape[s].G); }
@@ -123,135 +133,16 @@ __device__ __forceinline__ void issue_copy(const Task *__restrict__ tasks, int t
     }
 }
 
-// The chain of h reflectors on the RT rows in x, ascending or descending, in
-// blocks of kB with the Gram correction (the arithmetic of the staged kernel's
-// chain).  Granule indices i >= act (warp-uniform: the warp's columns there lie
-// past n) are neither read nor computed.  Per block: the reflector values and
-// tau are read at the block start, the dot products use one packed
-// accumulator per row, the kB * RT sums are reduced by one transposing warp
-// shuffle and one cross-warp combine, and the Gram entries are read after the
-// barrier (the shapes here hold more state per thread than the single-transform
-// kernel, and this order measured fastest for them).
-template <int G, int NG, int RT>
-__device__ __forceinline__ void tile_chain(float2 (&x)[RT][NG * 2], bool asc, int h,
-                                           const float *__restrict__ V, int64_t ldv,
-                                           const float *__restrict__ tau,
-                                           const float *__restrict__ gram, int t, int lane, int warp,
-                                           int rg, float *red, int &buf, int act) {
-    constexpr int RG = kThreads / G;
-    using C = staged::SCfg<G, NG, RT, RG, kB>;
-    constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L;
-    constexpr int KB = C::KEEP ? kB : 1;
-    for (int s = 0; s < h; s += kB) {
-        const int nb = h - s < kB ? h - s : kB;
-        int kk[kB];
-        float tk[kB];
-#pragma unroll
-        for (int j = 0; j < kB; ++j) {
-            kk[j] = asc ? s + j : h - 1 - s - j;
-            tk[j] = j < nb ? __ldg(tau + kk[j]) : 0.f;
-        }
-        float2 u[KB][E2];
-        auto load_u = [&](int j, float2(&dst)[E2]) {
-#pragma unroll
-            for (int i = 0; i < NG; ++i) {
-                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < nb && i < act)
-                    q = __ldg(reinterpret_cast<const float4 *>(V + (size_t)kk[j] * ldv) + (t + G * i));
-                dst[2 * i] = make_float2(q.x, q.y);
-                dst[2 * i + 1] = make_float2(q.z, q.w);
-            }
-        };
-        if constexpr (C::KEEP) {
-#pragma unroll
-            for (int j = 0; j < kB; ++j) load_u(j, u[j]);
-        }
-        float p[NV];
-#pragma unroll
-        for (int j = 0; j < kB; ++j) {
-            if constexpr (!C::KEEP) load_u(j, u[0]);
-            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
-            float2 a[RT];
-#pragma unroll
-            for (int r = 0; r < RT; ++r) a[r] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < NG; ++i) {
-                if (i >= act) break;
-#pragma unroll
-                for (int r = 0; r < RT; ++r) {
-                    a[r] = __ffma2_rn(x[r][2 * i], uj[2 * i], a[r]);
-                    a[r] = __ffma2_rn(x[r][2 * i + 1], uj[2 * i + 1], a[r]);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < RT; ++r) p[j * RT + r] = a[r].x + a[r].y;
-        }
-        float v = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
-        float z[NV];
-        if constexpr (NW == 1) {
-#pragma unroll
-            for (int q = 0; q < NV; ++q) z[q] = __shfl_sync(0xffffffffu, v, q * L);
-        } else {
-            if ((lane & (L - 1)) == 0) red[fused::red_index<RG, NV, NW>(buf, rg, lane / L, warp)] = v;
-            if constexpr (RG > 1)
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "n"(G) : "memory");
-            else
-                __syncthreads();
-            const int idx = lane / L, sub = lane & (L - 1);
-            float q = 0.f;
-#pragma unroll
-            for (int w = sub; w < NW; w += L) q += red[fused::red_index<RG, NV, NW>(buf, rg, idx, w)];
-#pragma unroll
-            for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
-#pragma unroll
-            for (int qq = 0; qq < NV; ++qq) z[qq] = __shfl_sync(0xffffffffu, q, qq * L);
-            buf ^= 1;
-        }
-        float c[kB][RT];
-#pragma unroll
-        for (int j = 0; j < kB; ++j)
-#pragma unroll
-            for (int r = 0; r < RT; ++r) c[j][r] = z[j * RT + r];
-#pragma unroll
-        for (int j = 0; j < kB; ++j) {
-#pragma unroll
-            for (int r = 0; r < RT; ++r) c[j][r] *= -tk[j];
-#pragma unroll
-            for (int i = j + 1; i < kB; ++i) {
-                const int lo = asc ? kk[j] : kk[i];
-                const float g = i < nb ? __ldg(gram + (size_t)lo * staged::kGramBand + (i - j)) : 0.f;
-#pragma unroll
-                for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], g, c[i][r]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kB; ++j) {
-            if constexpr (!C::KEEP) load_u(j, u[0]);
-            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
-#pragma unroll
-            for (int i = 0; i < NG; ++i) {
-                if (i >= act) break;
-#pragma unroll
-                for (int r = 0; r < RT; ++r) {
-                    const float2 cc = make_float2(c[j][r], c[j][r]);
-                    x[r][2 * i] = __ffma2_rn(uj[2 * i], cc, x[r][2 * i]);
-                    x[r][2 * i + 1] = __ffma2_rn(uj[2 * i + 1], cc, x[r][2 * i + 1]);
-                }
-            }
-        }
-    }
-}
-
-// One tile of the task in slot `slot` with shape (G, NG, RT): rows from the
-// stage into registers, the stage handed to the next tile's copy, the chain of
-// `mode`, and the rows stored.  Not inlined, so every shape gets its own
-// register allocation.  Returns the reduction-buffer parity.
-template <int G, int NG, int RT>
+// One tile of the task in slot `slot` with shape (G, NG, RT, B): rows from
+// the stage into registers, the stage handed to the next tile's copy, the
+// chain of `mode`, and the rows stored.  Not inlined, so every shape gets its
+// own register allocation.  Returns the reduction-buffer parity.
+template <int G, int NG, int RT, int B>
 __device__ __noinline__ int tile_body(const Task *__restrict__ tasks, int slot, int mode, int buf) {
     constexpr int RG = kThreads / G;
-    using C = staged::SCfg<G, NG, RT, RG, kB>;
+    using C = staged::SCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, ROWS = C::ROWS;
-    static_assert(ROWS * C::COVER * 4 == kStageBytes, "stage size");
+    static_assert(ROWS * C::COVER * 4 <= kStageBytes, "stage size");
     static_assert(2 * RG * C::NV * C::NW <= kRedFloats, "reduction buffer");
     const Task &tk = tasks[b_task[slot]];
     const int64_t tile = b_tile[slot];
@@ -291,14 +182,14 @@ __device__ __noinline__ int tile_body(const Task *__restrict__ tasks, int slot, 
     }
 
     const float *sign = tk.sign;
-    if (mode != HH_MODE_W && sign) staged::scale2_part<G, NG, RT, RG, kB>(x, sign, t, act);
+    if (mode != HH_MODE_W && sign) staged::scale2_part<G, NG, RT, RG, B>(x, sign, t, act);
     for (int half = 0; half < (mode == HH_MODE_SYM ? 2 : 1); ++half) {
-        if (half == 1) staged::scale2_part<G, NG, RT, RG, kB>(x, tk.d, t, act);
+        if (half == 1) staged::scale2_part<G, NG, RT, RG, B>(x, tk.d, t, act);
         const bool asc = mode != HH_MODE_W && half == 0;
-        tile_chain<G, NG, RT>(x, asc, tk.h, tk.V, tk.ldv, tk.tau, tk.gram, t, lane, warp, rg, b_red,
-                              buf, act);
+        staged::chain<G, NG, RT, RG, B, false, true>(x, asc, tk.h, tk.V, tk.ldv, tk.tau, tk.gram,
+                                                     t, lane, warp, rg, b_red, buf, nullptr, act);
     }
-    if (mode != HH_MODE_WT && sign) staged::scale2_part<G, NG, RT, RG, kB>(x, sign, t, act);
+    if (mode != HH_MODE_WT && sign) staged::scale2_part<G, NG, RT, RG, B>(x, sign, t, act);
 
     float *Y = tk.Y;
     const int64_t ldy = tk.ldy;
@@ -324,7 +215,7 @@ __device__ __noinline__ int tile_body(const Task *__restrict__ tasks, int slot, 
 // shape, X and Y 16-byte aligned with ldx % 4 == 0, V rows zero padded to
 // ldv >= round_up(n, 128); *counter == 0 at launch; kStageBytes of dynamic
 // shared memory.
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 batched_chain_kernel(const Task *__restrict__ tasks, const Item *__restrict__ items, int nitems,
                      int *__restrict__ counter, int mode, int *__restrict__ err) {
     const int tid = threadIdx.x;
@@ -353,13 +244,16 @@ batched_chain_kernel(const Task *__restrict__ tasks, const Item *__restrict__ it
         }
         phase ^= 1;
         switch (tasks[task].shape) {
-            case 0: buf = tile_body<32, 2, 8>(tasks, slot, mode, buf); break;
-            case 1: buf = tile_body<32, 4, 4>(tasks, slot, mode, buf); break;
-            case 2: buf = tile_body<32, 8, 2>(tasks, slot, mode, buf); break;
-            case 3: buf = tile_body<64, 4, 4>(tasks, slot, mode, buf); break;
-            case 4: buf = tile_body<64, 8, 2>(tasks, slot, mode, buf); break;
-            case 5: buf = tile_body<128, 4, 4>(tasks, slot, mode, buf); break;
-            default: buf = tile_body<256, 4, 4>(tasks, slot, mode, buf); break;
+            case 0: buf = tile_body<32, 1, 16, 2>(tasks, slot, mode, buf); break;
+            case 1: buf = tile_body<32, 2, 16, 2>(tasks, slot, mode, buf); break;
+            case 2: buf = tile_body<32, 4, 8, 2>(tasks, slot, mode, buf); break;
+            case 3: buf = tile_body<32, 8, 4, 2>(tasks, slot, mode, buf); break;
+            case 4: buf = tile_body<32, 8, 4, 4>(tasks, slot, mode, buf); break;
+            case 5: buf = tile_body<64, 4, 4, 4>(tasks, slot, mode, buf); break;
+            case 6: buf = tile_body<64, 8, 4, 2>(tasks, slot, mode, buf); break;
+            case 7: buf = tile_body<128, 4, 4, 4>(tasks, slot, mode, buf); break;
+            case 8: buf = tile_body<128, 8, 4, 2>(tasks, slot, mode, buf); break;
+            default: buf = tile_body<32, 4, 8, 4>(tasks, slot, mode, buf); break;
         }
         slot ^= 1;
     }
@@ -410,13 +304,15 @@ static std::map<std::pair<int64_t, int64_t>, TuneEntry> g_tune;
 
 static bool shape_fits(int s, int64_t n) { return s >= 0 && s < kNumShapes && n <= shape_cover(s); }
 
-// Fixed rule: the smallest cover of n with four rows per thread.
+// Fixed rule: the smallest cover of n with 128 floats of state per thread
+// (64 for n <= 128), two reflectors per round.
 static int default_shape(int64_t n) {
-    if (n <= 256) return 0;
-    if (n <= 512) return 1;
+    if (n <= 128) return 0;
+    if (n <= 256) return 1;
+    if (n <= 512) return 2;
     if (n <= 1024) return 3;
-    if (n <= 2048) return 5;
-    return 6;
+    if (n <= 2048) return 6;
+    return 8;
 }
 
 static int lookup_shape(int64_t n, int64_t h) {
@@ -454,6 +350,11 @@ struct Batch {
     cudaStream_t capture = nullptr;
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    // the last launch (its stream and completion event): a launch on another
+    // stream waits for it, since both use d_counter and d_tasks
+    cudaEvent_t done = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool launched = false;
 };
 
 static void free_batch(Batch *b) {
@@ -464,6 +365,7 @@ static void free_batch(Batch *b) {
     }
     if (b->capture) cudaStreamDestroy(b->capture);
     if (b->upload_done) cudaEventDestroy(b->upload_done);
+    if (b->done) cudaEventDestroy(b->done);
     cudaFreeHost(b->pinned);
     cudaFree(b->d_tasks);
     cudaFree(b->d_items);
@@ -582,6 +484,7 @@ static hh_status batch_create(Batch **out, int count, const hh_plan_t *plans, co
         (e = dev_malloc(&b->d_counter, sizeof(int))) || (e = dev_malloc(&b->d_err, sizeof(int))) ||
         (e = cudaMallocHost(&b->pinned, tbytes)) ||
         (e = cudaEventCreateWithFlags(&b->upload_done, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) ||
         (e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) ||
         (e = cudaMemset(b->d_err, 0, sizeof(int))) ||
         (b->nitems > 0 && (e = cudaMemcpy(b->d_items, sorted.data(), sizeof(Item) * sorted.size(),
@@ -661,6 +564,9 @@ static hh_status batch_apply(Batch *b, int mode, const void *const *X, const int
     if (b->nitems == 0) return HH_OK;  // nothing to launch
     hh_status st = batch_graph(b, mode);
     if (st) return st;
+    // the previous launch on another stream still owns the counter and the table
+    if (b->launched && b->last_stream != s && (e = cudaStreamWaitEvent(s, b->done, 0)))
+        return cuda_fail(e, "cross-stream ordering");
     if (changed) {
         // the staging buffer may still feed the previous upload
         if ((e = cudaEventSynchronize(b->upload_done))) return cuda_fail(e, "upload wait");
@@ -673,6 +579,9 @@ static hh_status batch_apply(Batch *b, int mode, const void *const *X, const int
         b->uploaded = true;
     }
     if ((e = cudaGraphLaunch(b->exec[mode], s))) return cuda_fail(e, "cudaGraphLaunch");
+    if ((e = cudaEventRecord(b->done, s))) return cuda_fail(e, "launch event");
+    b->last_stream = s;
+    b->launched = true;
     return HH_OK;
 }
 

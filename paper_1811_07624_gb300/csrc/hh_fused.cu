@@ -6,7 +6,7 @@ namespace hh {
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                                int64_t batch, int64_t n, const float *U, const float *tau, int64_t ldv, int h,
                                const float *gram, const float *sign, const float *d, int vec_ok,
-                               int *err, int num_sms, cudaStream_t st);
+                               int *err, int num_sms, cudaStream_t st, const int *start);
 cudaError_t fused_dispatch_f64(hh_mode mode, const double *X, int64_t ldx, double *Y,
                                int64_t ldy, int64_t batch, int64_t n, const double *U,
                                const double *tau, int64_t ldv, int h, const double *sign, const double *d,
@@ -23,7 +23,8 @@ hh_status fused_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, v
         e = fused_dispatch_f32(mode, (const float *)X, ldx, (float *)Y, ldy, batch, p->n,
                                (const float *)p->u, (const float *)p->tau_t, p->ldv, (int)p->h,
                                (const float *)p->gram, (const float *)p->sign,
-                               (const float *)p->d, vec_ok, p->err, p->num_sms, st);
+                               (const float *)p->d, vec_ok, p->err, p->num_sms, st,
+                               p->skip_prefix ? p->start : nullptr);
     else if (p->dtype == HH_F64)
         e = fused_dispatch_f64(mode, (const double *)X, ldx, (double *)Y, ldy, batch, p->n,
                                (const double *)p->u, (const double *)p->tau_t, p->ldv, (int)p->h, (const double *)p->sign,

@@ -43,7 +43,7 @@ namespace hh {
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                                int64_t batch, int64_t n, const float *U, const float *tau, int64_t ldv, int h,
                                const float *gram, const float *sign, const float *d, int vec_ok,
-                               int *err, int num_sms, cudaStream_t st) {
+                               int *err, int num_sms, cudaStream_t st, const int *start) {
     using namespace fused;
     const int ni = (int)n;
     // Aligned rows with n % 4 == 0: persistent blocked kernel, tiles prefetched
@@ -51,7 +51,7 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
     if (vec_ok && n % 4 == 0 && n <= 8192) {
 #define HH_STAGED(G, NG, RT, RG, B)                                                            \
     staged::launch<G, NG, RT, RG, B>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, \
-                                     d, err, num_sms, st)
+                                     d, err, num_sms, st, start)
         // (G, NG, RT, RG, B): 4 rows per thread where the register budget allows,
         // so each loaded reflector value feeds 8 FMAs; B reflectors per round;
         // 32 columns per thread where n is large enough to fill them.
@@ -61,7 +61,7 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
         if (n <= 1024) return HH_STAGED(HH_N1024_G, HH_N1024_NG, HH_N1024_RT, HH_N1024_RG, HH_N1024_B);
         if (n <= 2048) return HH_STAGED(HH_N2048_G, HH_N2048_NG, HH_N2048_RT, HH_N2048_RG, HH_N2048_B);
 #ifndef HH_NO_SPLIT
-        if (n > 2048 && n <= 4096 &&
+        if (n > 2048 && n <= 4096 && !start &&
             h <= split::max_h<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>())
             return split::launch<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>(
                 mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, d, err, st);

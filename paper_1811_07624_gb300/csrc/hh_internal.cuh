@@ -86,6 +86,9 @@ struct Plan {
     void *sign = nullptr;   // ldv, +-1 (one padded), or null
     double *tau = nullptr;  // h, tau_k = 2 / v_k^T v_k (0 for v_k = 0)
     double *vnorm = nullptr;// h, |v_k|
+    int *start = nullptr;   // h, first non-zero column of v_k (n for v_k = 0)
+    bool skip_prefix = false;  // F32 kernels skip zero prefixes (hh_plan_skip_prefix)
+    bool skip_auto = false;    // at create, the zero prefixes held >= 1/16 of U
     int *err = nullptr;     // device status word: a kernel's bounded wait expired (HH_ERR_TIMEOUT)
     int *upd = nullptr;     // device flag of the last hh_update's prepare kernels (bit 1: U, 2: d)
     int num_sms = 0;

@@ -17,24 +17,31 @@ template <typename T>
 __device__ inline double to_f64(T v) { return (double)v; }
 
 // One CTA per reflector: FP64 sum of squares (fixed-order tree), tau, |v|,
-// then the zero-padded copy in the compute type.
+// the first non-zero column (n for v = 0), then the zero-padded copy in the
+// compute type.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kPrepThreads)
 prepare_reflectors_kernel(const Tin *__restrict__ U, int64_t ldu, int64_t n, int64_t ldv,
                           Tout *__restrict__ u_out, double *__restrict__ tau,
                           Tout *__restrict__ tau_t, double *__restrict__ vnorm,
-                          int *__restrict__ flag) {
+                          int *__restrict__ start, int *__restrict__ flag) {
     __shared__ double red[kPrepThreads];
+    __shared__ int first;
     const int64_t k = blockIdx.x;
     const Tin *v = U + k * ldu;
+    if (threadIdx.x == 0) first = (int)n;
+    __syncthreads();
     double s = 0.0;
     bool finite = true;
+    int f = (int)n;
     for (int64_t j = threadIdx.x; j < n; j += kPrepThreads) {
         double x = to_f64(v[j]);
         finite &= isfinite(x);
         s += x * x;
+        if (x != 0.0 && j < f) f = (int)j;
     }
     if (!finite) atomicOr(flag, 1);
+    if (f < (int)n) atomicMin(&first, f);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = kPrepThreads / 2; w > 0; w >>= 1) {
@@ -47,6 +54,7 @@ prepare_reflectors_kernel(const Tin *__restrict__ U, int64_t ldu, int64_t n, int
         tau[k] = t;
         tau_t[k] = (Tout)t;
         vnorm[k] = sqrt(nn);
+        start[k] = first;
         if (!isfinite(nn)) atomicOr(flag, 1);
     }
     Tout *o = u_out + k * ldv;
@@ -102,7 +110,8 @@ hh_status prepare_typed(Plan *p, const void *U, int64_t ldu, const void *d, cons
                         int *flag, cudaStream_t st) {
     if (p->h > 0) {
         prepare_reflectors_kernel<T, T><<<(unsigned)p->h, kPrepThreads, 0, st>>>(
-            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, (T *)p->tau_t, p->vnorm, flag);
+            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, (T *)p->tau_t, p->vnorm, p->start,
+            flag);
         prepare_gram_kernel<T><<<dim3((unsigned)p->h, 16), kPrepThreads, 0, st>>>(
             (const T *)p->u, p->ldv, p->n, p->h, (T *)p->gram);
     }
@@ -128,7 +137,8 @@ template <typename T>
 hh_status update_typed(Plan *p, const void *U, int64_t ldu, const void *d, cudaStream_t st) {
     if (p->h > 0) {
         prepare_reflectors_kernel<T, T><<<(unsigned)p->h, kPrepThreads, 0, st>>>(
-            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, (T *)p->tau_t, p->vnorm, p->upd);
+            (const T *)U, ldu, p->n, p->ldv, (T *)p->u, p->tau, (T *)p->tau_t, p->vnorm, p->start,
+            p->upd);
         prepare_gram_kernel<T><<<dim3((unsigned)p->h, 16), kPrepThreads, 0, st>>>(
             (const T *)p->u, p->ldv, p->n, p->h, (T *)p->gram);
     }

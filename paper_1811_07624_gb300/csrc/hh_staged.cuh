@@ -30,6 +30,8 @@
 // the end without trusting its data.
 #pragma once
 
+#include <type_traits>
+
 #include "hh_fused.cuh"
 
 namespace hh {
@@ -146,13 +148,47 @@ __device__ __forceinline__ void scale2_part(float2 (&x)[RT][SCfg<G, NG, RT, RG, 
     }
 }
 
+// Dot products and update of one reflector over the granules i >= I0 (I0 a
+// compile-time count), in the same order as over all of them: one packed
+// accumulator per row, elements ascending.
+template <int I0, int RT, int E2>
+__device__ __forceinline__ void dot_from(const float2 (&x)[RT][E2], const float2 (&uj)[E2],
+                                         float *p) {
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 2 * I0; e < E2; ++e) a = __ffma2_rn(x[r][e], uj[e], a);
+        p[r] = a.x + a.y;
+    }
+}
+template <int I0, int RT, int E2>
+__device__ __forceinline__ void update_from(float2 (&x)[RT][E2], const float2 (&uj)[E2],
+                                            const float *c) {
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const float2 cc = make_float2(c[r], c[r]);
+#pragma unroll
+        for (int e = 2 * I0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
+    }
+}
 // Apply h reflectors to the RT rows in x, ascending (k = 0..h-1) or descending
-// (k = h-1..0), in blocks of B.
-template <int G, int NG, int RT, int RG, int B>
+// (k = h-1..0), in blocks of B.  With TR, start[k] is the first column where
+// v_k may be non-zero (the reflectors of a partial QR factorization, §II-D,
+// have k leading zeros): a block skips the granule indices i whose 4G columns
+// all lie before the smallest start of its reflectors, in the dot products
+// and in the update (a warp-uniform branch).  The skipped terms are exact
+// zeros, so the result is the same as without skipping.  With PART, granule
+// indices i >= act (warp-uniform: the warp's columns there lie past n) are
+// neither read nor computed, so a tile shape wider than n costs n columns of
+// arithmetic and reads nothing past the reflectors' rows (the batched launch).
+template <int G, int NG, int RT, int RG, int B, bool TR = false, bool PART = false>
 __device__ __forceinline__ void chain(
     float2 (&x)[RT][SCfg<G, NG, RT, RG, B>::E2], bool asc, int h, const float *__restrict__ V,
     int64_t ldv, const float *__restrict__ tau, const float *__restrict__ gram, int t, int lane,
-    int warp, int rg, float *red, int &buf) {
+    int warp, int rg, float *red, int &buf, const int *__restrict__ start = nullptr,
+    int act = NG) {
+    constexpr bool RANGED = TR || PART;
     using C = SCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L;
     // Values of reflector j of the block starting at s (zeros past h).
@@ -163,7 +199,7 @@ __device__ __forceinline__ void chain(
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ok) q = __ldg(row + (t + G * i));
+            if (ok && (!PART || i < act)) q = __ldg(row + (t + G * i));
             dst[2 * i] = make_float2(q.x, q.y);
             dst[2 * i + 1] = make_float2(q.z, q.w);
         }
@@ -198,79 +234,156 @@ __device__ __forceinline__ void chain(
             }
         }
     };
-    for (int s = 0; s < h; s += B) {
-        const int nb = h - s < B ? h - s : B;
-        float tk[B], gv[B][B];
-        load_coef(s, tk, gv);
-        auto load_u = [&](int j, float2(&dst)[E2]) { load_block_u(s, j, dst); };
-        float p[NV];
+    // One round of B reflectors starting at s; granule indices below the
+    // compile-time I0 are left out (zero-prefix skipping; 0 otherwise).
+    auto round = [&](auto i0c, int s) {
+        constexpr int I0 = decltype(i0c)::value;
+        (void)I0;
+            const int nb = h - s < B ? h - s : B;
+            float tk[B], gv[B][B];
+            load_coef(s, tk, gv);
+            auto load_u = [&](int j, float2(&dst)[E2]) { load_block_u(s, j, dst); };
+            float p[NV];
+    #pragma unroll
+            for (int j = 0; j < B; ++j) {
+                if constexpr (!C::KEEP) load_u(j, u[0]);
+                const float2(&uj)[E2] = u[C::KEEP ? j : 0];
+                if constexpr (TR && !PART) {
+                    dot_from<I0, RT, E2>(x, uj, p + j * RT);
+                } else if constexpr (RANGED) {
+                    // the same summation order per row, skipped granules left out
+                    float2 a[RT];
+    #pragma unroll
+                    for (int r = 0; r < RT; ++r) a[r] = make_float2(0.f, 0.f);
+    #pragma unroll
+                    for (int i = 0; i < NG; ++i) {
+                        if (PART && i >= act) continue;
+    #pragma unroll
+                        for (int r = 0; r < RT; ++r) {
+                            a[r] = __ffma2_rn(x[r][2 * i], uj[2 * i], a[r]);
+                            a[r] = __ffma2_rn(x[r][2 * i + 1], uj[2 * i + 1], a[r]);
+                        }
+                    }
+    #pragma unroll
+                    for (int r = 0; r < RT; ++r) p[j * RT + r] = a[r].x + a[r].y;
+                } else {
+                    // one packed accumulator per row
+    #pragma unroll
+                    for (int r = 0; r < RT; ++r) {
+                        float2 a = make_float2(0.f, 0.f);
+    #pragma unroll
+                        for (int e = 0; e < E2; ++e) a = __ffma2_rn(x[r][e], uj[e], a);
+                        p[j * RT + r] = a.x + a.y;
+                    }
+                }
+            }
+            float v = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
+            float z[NV];
+            if constexpr (NW == 1) {
+    #pragma unroll
+                for (int q = 0; q < NV; ++q) z[q] = __shfl_sync(0xffffffffu, v, q * L);
+            } else {
+                if ((lane & (L - 1)) == 0) red[fused::red_index<RG, NV, NW>(buf, rg, lane / L, warp)] = v;
+                // only this row group's warps meet here (named barrier 1 + rg with
+                // several groups), so row groups do not wait for one another
+                if constexpr (RG > 1)
+                    asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "n"(G) : "memory");
+                else
+                    __syncthreads();
+                const int idx = lane / L, sub = lane & (L - 1);
+                float q = 0.f;
+    #pragma unroll
+                for (int w = sub; w < NW; w += L) q += red[fused::red_index<RG, NV, NW>(buf, rg, idx, w)];
+    #pragma unroll
+                for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+    #pragma unroll
+                for (int qq = 0; qq < NV; ++qq) z[qq] = __shfl_sync(0xffffffffu, q, qq * L);
+                buf ^= 1;
+            }
+            // Coefficients in the order the reflectors act, stored negated:
+            // c_j = -tau_j (z_j - sum_{i<j} c_i g_ij), resolved left to right.  The
+            // Gram entries are uniform scalars read through L1 (the smaller index
+            // of each pair addresses the band).
+            float c[B][RT];
+    #pragma unroll
+            for (int j = 0; j < B; ++j)
+    #pragma unroll
+                for (int r = 0; r < RT; ++r) c[j][r] = z[j * RT + r];
+    #pragma unroll
+            for (int j = 0; j < B; ++j) {
+    #pragma unroll
+                for (int r = 0; r < RT; ++r) c[j][r] *= -tk[j];
+    #pragma unroll
+                for (int i = j + 1; i < B; ++i) {
+    #pragma unroll
+                    for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], gv[j][i], c[i][r]);
+                }
+            }
+    #pragma unroll
+            for (int j = 0; j < B; ++j) {
+                if constexpr (!C::KEEP) load_u(j, u[0]);
+                const float2(&uj)[E2] = u[C::KEEP ? j : 0];
+                if constexpr (TR && !PART) {
+                    float cj[RT];
+    #pragma unroll
+                    for (int r = 0; r < RT; ++r) cj[r] = c[j][r];
+                    update_from<I0, RT, E2>(x, uj, cj);
+                } else if constexpr (RANGED) {
+    #pragma unroll
+                    for (int i = 0; i < NG; ++i) {
+                        if (PART && i >= act) continue;
+    #pragma unroll
+                        for (int r = 0; r < RT; ++r) {
+                            const float2 cc = make_float2(c[j][r], c[j][r]);
+                            x[r][2 * i] = __ffma2_rn(uj[2 * i], cc, x[r][2 * i]);
+                            x[r][2 * i + 1] = __ffma2_rn(uj[2 * i + 1], cc, x[r][2 * i + 1]);
+                        }
+                    }
+                } else {
+    #pragma unroll
+                    for (int r = 0; r < RT; ++r) {
+                        const float2 cc = make_float2(c[j][r], c[j][r]);
+    #pragma unroll
+                        for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
+                    }
+                }
+                if constexpr (C::KEEP) load_block_u(s + B, j, u[j]);
+            }
+    };
+    if constexpr (TR && !PART) {
+        static_assert(NG <= 8, "zero-prefix skipping covers at most 8 granule indices");
+        // Rounds are taken in runs with the same skipped prefix, each run by an
+        // instantiation for its prefix, so the loops stay fully unrolled.
+        auto i0_of = [&](int s0) {
+            int mn = 0x7fffffff;
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-            if constexpr (!C::KEEP) load_u(j, u[0]);
-            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
-            // one packed accumulator per row
-#pragma unroll
-            for (int r = 0; r < RT; ++r) {
-                float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int e = 0; e < E2; ++e) a = __ffma2_rn(x[r][e], uj[e], a);
-                p[j * RT + r] = a.x + a.y;
+            for (int j = 0; j < B; ++j)
+                if (s0 + j < h) {
+                    const int st0 = __ldg(start + (asc ? s0 + j : h - 1 - s0 - j));
+                    mn = st0 < mn ? st0 : mn;
+                }
+            const int q = mn / (4 * G);
+            return q < NG ? q : NG;
+        };
+        int s = 0;
+        while (s < h) {
+            const int i0 = i0_of(s);
+            int e = s + B;
+            while (e < h && i0_of(e) == i0) e += B;
+            switch (i0) {
+#define HH_RUN_CASE(I)                                                                   \
+    case I:                                                                              \
+        if constexpr (I <= NG)                                                           \
+            for (; s < e; s += B) round(std::integral_constant<int, (I <= NG ? I : 0)>{}, s); \
+        break;
+                HH_RUN_CASE(0) HH_RUN_CASE(1) HH_RUN_CASE(2) HH_RUN_CASE(3) HH_RUN_CASE(4)
+                HH_RUN_CASE(5) HH_RUN_CASE(6) HH_RUN_CASE(7) HH_RUN_CASE(8)
+#undef HH_RUN_CASE
+                default: s = e; break;
             }
         }
-        float v = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
-        float z[NV];
-        if constexpr (NW == 1) {
-#pragma unroll
-            for (int q = 0; q < NV; ++q) z[q] = __shfl_sync(0xffffffffu, v, q * L);
-        } else {
-            if ((lane & (L - 1)) == 0) red[fused::red_index<RG, NV, NW>(buf, rg, lane / L, warp)] = v;
-            // only this row group's warps meet here (named barrier 1 + rg with
-            // several groups), so row groups do not wait for one another
-            if constexpr (RG > 1)
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + rg), "n"(G) : "memory");
-            else
-                __syncthreads();
-            const int idx = lane / L, sub = lane & (L - 1);
-            float q = 0.f;
-#pragma unroll
-            for (int w = sub; w < NW; w += L) q += red[fused::red_index<RG, NV, NW>(buf, rg, idx, w)];
-#pragma unroll
-            for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
-#pragma unroll
-            for (int qq = 0; qq < NV; ++qq) z[qq] = __shfl_sync(0xffffffffu, q, qq * L);
-            buf ^= 1;
-        }
-        // Coefficients in the order the reflectors act, stored negated:
-        // c_j = -tau_j (z_j - sum_{i<j} c_i g_ij), resolved left to right.  The
-        // Gram entries are uniform scalars read through L1 (the smaller index
-        // of each pair addresses the band).
-        float c[B][RT];
-#pragma unroll
-        for (int j = 0; j < B; ++j)
-#pragma unroll
-            for (int r = 0; r < RT; ++r) c[j][r] = z[j * RT + r];
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-#pragma unroll
-            for (int r = 0; r < RT; ++r) c[j][r] *= -tk[j];
-#pragma unroll
-            for (int i = j + 1; i < B; ++i) {
-#pragma unroll
-                for (int r = 0; r < RT; ++r) c[i][r] = fmaf(c[j][r], gv[j][i], c[i][r]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            if constexpr (!C::KEEP) load_u(j, u[0]);
-            const float2(&uj)[E2] = u[C::KEEP ? j : 0];
-#pragma unroll
-            for (int r = 0; r < RT; ++r) {
-                const float2 cc = make_float2(c[j][r], c[j][r]);
-#pragma unroll
-                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(uj[e], cc, x[r][e]);
-            }
-            if constexpr (C::KEEP) load_block_u(s + B, j, u[j]);
-        }
+    } else {
+        for (int s = 0; s < h; s += B) round(std::integral_constant<int, 0>{}, s);
     }
 }
 
@@ -279,12 +392,13 @@ __device__ __forceinline__ void chain(
 // == 0, ROWS*n floats of dynamic shared memory.
 // Registers: at most 128 per thread (16 resident warps per SM), or 255 for wide
 // tiles (8 warps per SM).
-template <int MODE, int G, int NG, int RT, int RG, int B>
+template <int MODE, int G, int NG, int RT, int RG, int B, bool TR = false>
 __global__ void __launch_bounds__(G *RG, (SCfg<G, NG, RT, RG, B>::MINB))
 staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t batch, int n,
                     const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv,
                     int h, const float *__restrict__ gram, const float *__restrict__ sign,
-                    const float *__restrict__ d, int *__restrict__ err) {
+                    const float *__restrict__ d, int *__restrict__ err,
+                    const int *__restrict__ start) {
     using C = SCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, ROWS = C::ROWS;
     extern __shared__ __align__(128) float stage[];  // ROWS x n
@@ -355,7 +469,8 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
         for (int half = 0; half < (MODE == HH_MODE_SYM ? 2 : 1); ++half) {
             if (half == 1) scale2<G, NG, RT, RG, B>(x, d, t);
             const bool asc = MODE != HH_MODE_W && half == 0;
-            chain<G, NG, RT, RG, B>(x, asc, h, V, ldv, tau, gram, t, lane, warp, rg, red, buf);
+            chain<G, NG, RT, RG, B, TR>(x, asc, h, V, ldv, tau, gram, t, lane, warp, rg, red, buf,
+                                        start);
         }
         if (MODE != HH_MODE_WT && sign) scale2<G, NG, RT, RG, B>(x, sign, t);
 
@@ -376,21 +491,23 @@ staged_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t 
     }
 }
 
+// start: per-reflector first possibly non-zero column, or null; with it the
+// kernels skip zero prefixes (TR).
 template <int G, int NG, int RT, int RG, int B>
 cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                    int64_t batch, int n, const float *V, const float *tau, int64_t ldv, int h,
                    const float *gram, const float *sign, const float *d, int *err, int num_sms,
-                   cudaStream_t st) {
+                   cudaStream_t st, const int *start = nullptr) {
     using C = SCfg<G, NG, RT, RG, B>;
     const size_t smem = (size_t)C::ROWS * n * sizeof(float);
     const int64_t tiles = (batch + C::ROWS - 1) / C::ROWS;
     // Per kernel (one entry per mode) and device: the shared-memory opt-in at
     // the largest stage this configuration can need, and the resident CTAs per
     // SM there (a lower bound for smaller stages), both set on first use.
-    static PerDevice state[3];
-    auto run = [&](auto kern) -> cudaError_t {
+    static PerDevice state[6];
+    auto run = [&](auto kern, int slot) -> cudaError_t {
         int per_sm = 1;
-        cudaError_t e = per_device(state[mode], per_sm, [&](int &v) -> cudaError_t {
+        cudaError_t e = per_device(state[slot], per_sm, [&](int &v) -> cudaError_t {
             const size_t smax = (size_t)C::ROWS * C::COVER * sizeof(float);
             cudaError_t e2 =
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
@@ -405,13 +522,20 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
         const int64_t slots = (int64_t)num_sms * per_sm;
         const int grid = (int)(tiles < slots ? tiles : slots);
         kern<<<grid, C::THREADS, smem, st>>>(X, ldx, Y, ldy, batch, n, V, tau, ldv, h, gram, sign,
-                                             d, err);
+                                             d, err, start);
         return cudaGetLastError();
     };
+    if (start) {
+        switch (mode) {
+            case HH_MODE_W: return run(staged_chain_kernel<HH_MODE_W, G, NG, RT, RG, B, true>, 3);
+            case HH_MODE_WT: return run(staged_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B, true>, 4);
+            default: return run(staged_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B, true>, 5);
+        }
+    }
     switch (mode) {
-        case HH_MODE_W: return run(staged_chain_kernel<HH_MODE_W, G, NG, RT, RG, B>);
-        case HH_MODE_WT: return run(staged_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B>);
-        default: return run(staged_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B>);
+        case HH_MODE_W: return run(staged_chain_kernel<HH_MODE_W, G, NG, RT, RG, B>, 0);
+        case HH_MODE_WT: return run(staged_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B>, 1);
+        default: return run(staged_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B>, 2);
     }
 }
 

@@ -103,12 +103,12 @@ def test_batched_ragged_matches_oracle(mode):
     batch.close()
 
 
-@pytest.mark.parametrize("shape", range(7))
+@pytest.mark.parametrize("shape", range(10))
 def test_every_tile_shape(shape):
     """Each compiled shape, at its full cover, one granule short, and ragged."""
     hh = _hh()
     shapes = hh.batch_shapes()
-    assert len(shapes) == 7
+    assert len(shapes) == 10
     cover = shapes[shape]["cover"]
     ns = sorted({cover, max(4, cover - 64), max(4, cover // 2 + 4), max(4, cover - 124)})
     specs = [(n, h, b, 100 + 10 * shape + j)
