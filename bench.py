@@ -5,16 +5,24 @@ synthetic vectors (inputs larger than L2, so no flush is needed):
 
   chain_W, chain_WT, chain_SYM   FP32 chain, n=4096, h=16, 262,144 vectors:
                                  y = sigma.*(W x), W^T(sigma.*x), sigma.*W(d.*W^T(sigma.*x))
+  c2_n<n>_h<h>_<W|WT|SYM>        the same three applies at scale: n=1024, h in {10, 32},
+                                 1,048,576 vectors; n=4096, h in {12, 64}, 262,144 vectors
   wy_h64, wy_h256, wy_h1024      BF16 compact-WY (tcgen05), n=4096, 262,144 vectors, y = W x
   mahalanobis                    FP32 fast Mahalanobis distance, n=256, h=16, 1,048,576 pairs
   mahalanobis_grad               its gradient w.r.t. U and d (metric-learning loss)
   adjoint_SYM                    FP32 forward + adjoint of S x, n=1024, h=32, 65,536 vectors
+  trunc_qr                       Result 3's partial-QR reflectors (k - 1 leading zeros), n=1024,
+                                 h=512, 262,144 vectors, zero prefixes skipped (timed beside
+                                 the same apply without skipping)
   batched_C5                     512 independent FP32 transforms, n in {128..2048}, h in
                                  [4, 64], 1,024-16,384 vectors each, y = W x, in ONE
                                  persistent graph-replayed launch (autotuned tile shapes)
 
 `value` is vectors per second through the whole step (the sum of the rows'
-vectors over the step time), timed with CUDA events on the launching stream.
+vectors over the step time, vectors of mixed n; a Mahalanobis pair counts as
+the one difference vector it transforms), timed with CUDA events on the
+launching stream.  The "c2" object gives the same rate over the FP32-chain-at-
+scale rows alone.
 Each row also reports its own time, vectors/s, algorithmic GB/s and FLOP/s
 and roofline fraction; the FP32 chain on the WY rows' shapes and data is
 timed beside them ("BF16-WY vs FP32 plain"), and the 512 transforms of
@@ -52,17 +60,28 @@ C5_COUNT, C5_SCALE = 512, 1.0
 C5_TUNE_H, C5_TUNE_ROWS = [4, 8, 16, 32, 64], 32_768
 E2E_CHUNKS = 16    # chunks per large row in the pipelined end-to-end step
 TUNE_TABLE = None  # --tune-table: load the batched launch's shapes from here, or tune and save
-ALL_ROWS = ["chain_W", "chain_WT", "chain_SYM", "wy_h64", "wy_h256", "wy_h1024", "mahalanobis",
-            "mahalanobis_grad", "adjoint_SYM", "batched_C5"]
+# the FP32 chain at the configurations of the "plain FP32 chain at scale" workload:
+# (n, h, batch) for each of W, W^T and S
+C2_SHAPES = [(1024, 10, 1_048_576), (1024, 32, 1_048_576), (4096, 12, 262_144), (4096, 64, 262_144)]
+C2_ROWS = [f"c2_n{n}_h{h}_{m}" for n, h, _ in C2_SHAPES for m in ("W", "WT", "SYM")]
+ALL_ROWS = (["chain_W", "chain_WT", "chain_SYM"] + C2_ROWS
+            + ["wy_h64", "wy_h256", "wy_h1024", "mahalanobis", "mahalanobis_grad", "adjoint_SYM",
+               "batched_C5", "trunc_qr"])
 
-KERNEL_SOURCES = ["paper_1811_07624_gb300/csrc/hh_staged.cuh",
-                  "paper_1811_07624_gb300/csrc/hh_fused_f32.cu",
-                  "paper_1811_07624_gb300/csrc/hh_fused.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "staged_chain_n4096_h16_ncu_full.md")
-BATCHED_SOURCES = ["paper_1811_07624_gb300/csrc/hh_batched.cu",
-                   "paper_1811_07624_gb300/csrc/hh_staged.cuh",
-                   "paper_1811_07624_gb300/csrc/hh_fused.cuh"]
-BATCHED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "batched_c5_ncu_full.md")
+_CSRC = "paper_1811_07624_gb300/csrc/"
+_CHAIN_SRC = [_CSRC + f for f in ("hh_split.cuh", "hh_staged.cuh", "hh_fused.cuh",
+                                  "hh_fused_f32.cu")]
+# kernel sources behind each row kind: a traffic figure is used only while they
+# hash to the value recorded with it
+ROW_SOURCES = {
+    "chain": _CHAIN_SRC, "c2": _CHAIN_SRC,
+    "wy": [_CSRC + "hh_wy.cu", _CSRC + "hh_tc.cuh"],
+    "mahalanobis": [_CSRC + "hh_mahalanobis.cu", _CSRC + "hh_backward.cu", _CSRC + "hh_fused.cuh"],
+    "adjoint": [_CSRC + "hh_backward.cu", _CSRC + "hh_fused.cuh"] + _CHAIN_SRC,
+    "batched": [_CSRC + "hh_batched.cu", _CSRC + "hh_staged.cuh", _CSRC + "hh_fused.cuh"],
+    "trunc": _CHAIN_SRC,
+}
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 def dist_env():
@@ -79,24 +98,84 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "of fallback"
 
 
-def profiled_traffic(mode, batch, sources=None, path=None):
-    """DRAM bytes of one launch from a committed ncu summary, scaled by the
-    vector count; None when the kernel sources changed since the capture."""
-    sources = sources or KERNEL_SOURCES
-    path = path or TRAFFIC_FILE
+def sources_sha(files):
     h = hashlib.sha256()
-    for f in sources:
+    for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    sha = h.hexdigest()[:16]
+    return h.hexdigest()[:16]
+
+
+def row_kind(name):
+    return name.split("_")[0]
+
+
+def profiled_traffic(row, units, path=None):
+    """DRAM bytes (read + write) of one launch of `row` over `units` vectors, from
+    the ncu figures recorded in profiles/traffic.json, scaled by units; None
+    when there is no figure or the row's kernel sources changed since."""
+    path = path or TRAFFIC_JSON
     if not os.path.exists(path):
         return None
-    for line in open(path):
-        if line.startswith("TRAFFIC ") and f"mode={mode} " in line:
-            kv = dict(t.split("=", 1) for t in line.split()[1:])
-            if kv.get("sources_sha256") == sha:
-                return float(kv["bytes_per_vector"]) * batch
+    with open(path) as f:
+        entries = json.load(f).get("entries", [])
+    for e in entries:
+        if e.get("row") != row:
+            continue
+        if e.get("sources_sha256") != sources_sha(ROW_SOURCES[row_kind(row)]):
+            return None
+        return (float(e["dram_read_bytes"]) + float(e["dram_write_bytes"])) * units / e["units"]
     return None
+
+
+_NCU_UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+
+
+def ncu_dram_bytes(csv_path):
+    """[(read, write)] DRAM bytes of each launch, in launch order, in an ncu --csv
+    log of dram__bytes_read.sum and dram__bytes_write.sum."""
+    text = open(csv_path).read()
+    start = text.find('"ID"')
+    if start < 0:
+        raise ValueError(f"{csv_path}: no ncu CSV table")
+    order, got = [], {}
+    for row in csv.DictReader(io.StringIO(text[start:])):
+        name = row["Metric Name"]
+        if name not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        if row["ID"] not in got:
+            order.append(row["ID"])
+            got[row["ID"]] = {}
+        val = float(row["Metric Value"].replace(",", ""))
+        got[row["ID"]][name] = val * _NCU_UNITS[row["Metric Unit"]]
+    return [(got[i]["dram__bytes_read.sum"], got[i]["dram__bytes_write.sum"]) for i in order]
+
+
+def ingest_traffic(csv_path, rows, out_path, command):
+    """Record the DRAM bytes of the launches captured in an ncu log: launch i is
+    the first launch of rows[i] (each at its full batch)."""
+    entries = []
+    if os.path.exists(out_path):
+        with open(out_path) as f:
+            entries = json.load(f).get("entries", [])
+    launches = ncu_dram_bytes(csv_path)
+    if len(launches) < len(rows):
+        raise ValueError(f"{csv_path}: {len(launches)} launches for {len(rows)} rows")
+    full = step_vectors(rows)
+    for row, (rd, wr) in zip(rows, launches):
+        entries = [e for e in entries if e.get("row") != row]
+        entries.append({"row": row, "units": full[row], "dram_read_bytes": rd,
+                        "dram_write_bytes": wr, "sources": ROW_SOURCES[row_kind(row)],
+                        "sources_sha256": sources_sha(ROW_SOURCES[row_kind(row)]),
+                        "command": command})
+    entries.sort(key=lambda e: e["row"])
+    with open(out_path, "w") as f:
+        json.dump({"about": "DRAM bytes of one launch per row (ncu dram__bytes_read.sum and "
+                            "dram__bytes_write.sum, one pass, --clock-control none), at the "
+                            "row's full batch; bench.py uses a figure only while the row's "
+                            "kernel sources hash to sources_sha256",
+                   "entries": entries}, f, indent=1)
+        f.write("\n")
 
 
 class ClockSampler:
@@ -176,11 +255,12 @@ _CHAIN_ROWS = []
 
 
 class ChainRow:
-    def __init__(self, torch, dev, mode, n, h, batch, seed=0):
+    def __init__(self, torch, dev, mode, n, h, batch, seed=0, name=None):
         import synthetic_inputs as si
         from paper_1811_07624_gb300 import Plan
 
-        self.name, self.mode, self.n, self.h, self.B = f"chain_{mode}", mode, n, h, batch
+        self.name = name or f"chain_{mode}"
+        self.mode, self.n, self.h, self.B = mode, n, h, batch
         self.U = si.reflectors(n, h, seed=seed)
         self.d = si.spectrum(n, seed=seed)
         self.s = si.sign(n, seed=seed)
@@ -188,11 +268,14 @@ class ChainRow:
                          d=torch.tensor(self.d, device=dev, dtype=torch.float32),
                          sign=torch.tensor(self.s, device=dev))
         key = (n, batch, seed)
-        if key not in _SHARED:  # the three chain rows read the same vectors
+        if key not in _SHARED:  # the chain rows of one (n, batch) read the same vectors
             g = torch.Generator(device=dev).manual_seed(seed + 1)
             _SHARED[key] = torch.randn(batch, n, device=dev, generator=g)
+            _SHARED[("Y",) + key] = torch.empty_like(_SHARED[key])
         self.X = _SHARED[key]
-        self.Y = torch.empty_like(self.X)
+        # ... and write one output buffer (each row's parity is read right after
+        # its own first call)
+        self.Y = _SHARED[("Y",) + key]
         self.torch = torch
         self.launches = 1
         self.bound = "hbm" if (self.flops() / self.bytes()) < 11.9 else "alu"
@@ -222,29 +305,36 @@ class ChainRow:
         return rel_l2(self.Y[idx].double().cpu().numpy(), ref)
 
     def e2e(self, torch):
-        # The three chain rows apply W, W^T and S to the same vectors (as in the
-        # device-resident step): the first of them copies the vectors in once
-        # and runs all three per chunk; the others add nothing.
+        # The chain rows of one (n, batch) transform the same vectors (as in the
+        # device-resident step): the first of them copies the vectors in once and
+        # runs every row on each chunk; the others add nothing.  Each row's
+        # results go through a ring of two chunk buffers on the device and on the
+        # host; chunk c reuses the buffers of chunk c - 2 once their copy out has
+        # finished (the pipeline's per-key ordering).
         key = ("e2e", self.n, self.B)
         if key in _SHARED:
             return 0, 0, []
-        modes = [r for r in _CHAIN_ROWS if (r.n, r.B) == (self.n, self.B)]
+        rows = [r for r in _CHAIN_ROWS if (r.n, r.B) == (self.n, self.B)]
         _SHARED[key] = True
         Xh = pinned_copy(torch, self.X)
         Xd = torch.empty_like(self.X)
-        outs = [(r, torch.empty(Xh.shape, dtype=Xh.dtype, pin_memory=True), torch.empty_like(self.X))
-                for r in modes]
+        spans = row_chunks(self.B, E2E_CHUNKS)
+        rows_max = max(b - a for a, b in spans)
+        ring = [[(torch.empty(rows_max, self.n, device=self.X.device),
+                  torch.empty(rows_max, self.n, pin_memory=True)) for _ in range(2)] for _ in rows]
         chunks = []
-        for r0, r1 in row_chunks(self.B, E2E_CHUNKS):
-            def comp(a=r0, b=r1):
-                for r, _, Yd in outs:
-                    r.plan.apply_mode(r.mode, Xd[a:b], out=Yd[a:b])
+        for c, (r0, r1) in enumerate(spans):
+            def comp(a=r0, b=r1, c=c):
+                for r, slots in zip(rows, ring):
+                    r.plan.apply_mode(r.mode, Xd[a:b], out=slots[c % 2][0][:b - a])
 
-            def cout(a=r0, b=r1):
-                for _, Yh, Yd in outs:
-                    Yh[a:b].copy_(Yd[a:b], non_blocking=True)
-            chunks.append((lambda a=r0, b=r1: Xd[a:b].copy_(Xh[a:b], non_blocking=True), comp, cout))
-        return Xh.numel() * 4, Xh.numel() * 4 * len(outs), chunks
+            def cout(a=r0, b=r1, c=c):
+                for slots in ring:
+                    Yd, Yh = slots[c % 2]
+                    Yh[:b - a].copy_(Yd[:b - a], non_blocking=True)
+            chunks.append((lambda a=r0, b=r1: Xd[a:b].copy_(Xh[a:b], non_blocking=True), comp, cout,
+                           ("chain ring", self.n, self.B, c % 2)))
+        return Xh.numel() * 4, Xh.numel() * 4 * len(rows), chunks
 
 
 class WYRow:
@@ -455,6 +545,91 @@ class AdjointRow:
         return (Xh.numel() + Gh.numel()) * 4, gUh.numel() * 4, [(h2d, comp, d2h)]
 
 
+N_TRQ, H_TRQ, B_TRQ = 1024, 512, 262_144
+
+
+class TruncRow:
+    """Result 3's partial-QR reflectors (§II-D) of a random orthonormal U: j_k has
+    k - 1 leading zeros, and the plan skips them (4(n - k + 1) per reflector).
+    y = J_1 ... J_h D x (apply_T of the plan of the reversed reflectors, sign D)."""
+
+    def __init__(self, torch, dev, seed=0):
+        import synthetic_inputs as si
+        from paper_1811_07624_gb300 import factor
+
+        self.name, self.torch = "trunc_qr", torch
+        self.n, self.h, self.B = N_TRQ, H_TRQ, B_TRQ
+        Q = si.random_orthonormal(self.n, seed + 31)
+        R, d, _ = factor.result3(Q, self.h)
+        self.R, self.d = R, d
+        self.plan, self.mode = factor.plan("result3", R, d, device=dev, dtype=torch.float32)
+        self.skip_auto = self.plan.skip_prefix()
+        g = torch.Generator(device=dev).manual_seed(seed + 32)
+        self.X = torch.randn(self.B, self.n, device=dev, generator=g)
+        self.Y = torch.empty_like(self.X)
+        self.launches = 1
+        self.bound = "alu"
+        # first non-zero column of each reflector of the plan (reversed order)
+        Rr = R.flip(0).float().numpy()
+        self.starts = [int(np.flatnonzero(r)[0]) if np.any(r) else self.n for r in Rr]
+
+    def vectors(self):
+        return self.B
+
+    def bytes(self):
+        return 2.0 * self.B * self.n * 4 + sum(self.n - s for s in self.starts) * 4
+
+    def flops(self):
+        return 4.0 * sum(self.n - s for s in self.starts) * self.B
+
+    def run(self):
+        self.plan.apply_mode(self.mode, self.X, out=self.Y)
+
+    def parity(self):
+        import oracle
+
+        t = self.torch
+        idx = t.linspace(0, self.B - 1, 64, device=self.X.device).long()
+        Rr = self.R.flip(0).float().double().numpy()
+        ref = oracle.apply("WT", Rr, self.X[idx].double().cpu().numpy(),
+                           sign=self.d.numpy().astype(np.int8))
+        return rel_l2(self.Y[idx].double().cpu().numpy(), ref)
+
+    def compare(self):
+        """The same apply with the skipping turned off (every reflector over all n)."""
+        t = self.torch
+
+        def timed(reps=3):
+            self.run()
+            t.cuda.synchronize()
+            a, b = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                self.run()
+            b.record()
+            t.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+        on = timed()
+        self.plan.skip_prefix(0)
+        off = timed()
+        self.plan.skip_prefix(-1)
+        full = 4.0 * self.n * self.h * self.B
+        return {"skip_ms": on, "no_skip_ms": off, "speedup": off / on,
+                "work_fraction": self.flops() / full, "skip_chosen_at_create": self.skip_auto}
+
+    def e2e(self, torch):
+        Xh = pinned_copy(torch, self.X)
+        Yh = torch.empty(Xh.shape, dtype=Xh.dtype, pin_memory=True)
+        Xd, Yd = torch.empty_like(self.X), torch.empty_like(self.X)
+        chunks = []
+        for r0, r1 in row_chunks(self.B, E2E_CHUNKS):
+            chunks.append((lambda a=r0, b=r1: Xd[a:b].copy_(Xh[a:b], non_blocking=True),
+                           lambda a=r0, b=r1: self.plan.apply_mode(self.mode, Xd[a:b],
+                                                                   out=Yd[a:b]),
+                           lambda a=r0, b=r1: Yh[a:b].copy_(Yd[a:b], non_blocking=True)))
+        return Xh.numel() * 4, Yh.numel() * 4, chunks
+
+
 def c5_specs():
     """The 512 transforms: (n, h, batch, seed), batches scaled by --batch-scale."""
     import synthetic_inputs as si
@@ -503,7 +678,7 @@ class BatchedRow:
         shapes = hh.batch_shapes()
         self.info = {"items": info["items"], "grid": info["grid"], "tune_s": self.tune_s,
                      "tune": self.tune_source,
-                     "shape_use": {f"G{shapes[k]['G']}xNG{shapes[k]['NG']}xRT{shapes[k]['RT']}":
+                     "shape_use": {f"{k}:G{shapes[k]['G']}xNG{shapes[k]['NG']}xRT{shapes[k]['RT']}":
                                    info["shapes"].count(k) for k in sorted(set(info["shapes"]))}}
 
     def vectors(self):
@@ -598,6 +773,9 @@ def make_rows(torch, dev, names):
     for nm in names:
         if nm.startswith("chain_"):
             rows.append(ChainRow(torch, dev, nm.split("_")[1], N_CHAIN, H_CHAIN, B_CHAIN))
+        elif nm.startswith("c2_"):
+            n, h, b, mode = c2_shape(nm)
+            rows.append(ChainRow(torch, dev, mode, n, h, b, name=nm))
         elif nm.startswith("wy_h"):
             rows.append(WYRow(torch, dev, N_CHAIN, int(nm[4:]), B_WY))
         elif nm == "mahalanobis":
@@ -608,26 +786,45 @@ def make_rows(torch, dev, names):
             rows.append(AdjointRow(torch, dev))
         elif nm == "batched_C5":
             rows.append(BatchedRow(torch, dev))
+        elif nm == "trunc_qr":
+            rows.append(TruncRow(torch, dev))
         else:
             raise ValueError(f"unknown row {nm}")
     return rows
 
 
+def c2_shape(name):
+    """(n, h, batch, mode) of a row named c2_n<n>_h<h>_<mode>."""
+    _, ns, hs, mode = name.split("_")
+    n, h = int(ns[1:]), int(hs[1:])
+    for n2, h2, b in C2_SHAPES:
+        if (n2, h2) == (n, h):
+            return n, h, b, mode
+    raise ValueError(f"unknown row {name}")
+
+
 def scale_batches(f):
-    global B_CHAIN, B_WY, P_MAHAL, B_ADJ, C5_SCALE
+    global B_CHAIN, B_WY, P_MAHAL, B_ADJ, C5_SCALE, C2_SHAPES, B_TRQ
+    B_TRQ = max(1, int(B_TRQ * f))
+    C2_SHAPES = [(n, h, max(1, int(b * f))) for n, h, b in C2_SHAPES]
     B_CHAIN, B_WY = max(1, int(B_CHAIN * f)), max(1, int(B_WY * f))
     P_MAHAL, B_ADJ = max(1, int(P_MAHAL * f)), max(1, int(B_ADJ * f))
     C5_SCALE = f
 
 
 def config_dict(names):
+    c2 = ", ".join(f"n={n} h={h} batch={b}" for n, h, b in C2_SHAPES)
     return {"workload": "Householder-chain hot path, one step = every row once: FP32 chain "
-                        f"n={N_CHAIN} h={H_CHAIN} batch={B_CHAIN} (W, W^T, S); BF16 compact-WY "
+                        f"n={N_CHAIN} h={H_CHAIN} batch={B_CHAIN} (W, W^T, S); FP32 chain at "
+                        f"scale {c2} (W, W^T, S each); BF16 compact-WY "
                         f"n={N_CHAIN} h=64/256/1024 batch={B_WY} (W); fast Mahalanobis n={N_MAHAL} "
                         f"h={H_MAHAL} {P_MAHAL} pairs (+ gradient); adjoint of S n={N_ADJ} "
                         f"h={H_ADJ} batch={B_ADJ}; {C5_COUNT} ragged FP32 transforms (n 128-2048, "
                         f"h 4-64, batch 1024-16384 x {C5_SCALE:g}) in one batched launch",
             "rows": list(names), "l2": "every row's inputs are larger than L2 (no flush)",
+            "value_counts": "vectors transformed per second over the whole step, mixed n: a "
+                            "Mahalanobis pair counts as the one difference vector it transforms; "
+                            "each row's own rate and roofline fraction is under rows",
             "parallelism": "replicas (one independent copy per rank)"}
 
 
@@ -643,13 +840,15 @@ def oracle_units(names):
 
     fns = {}
     for nm in names:
-        if nm.startswith("chain_"):
-            mode = nm.split("_")[1]
-            U, d, s = (si.reflectors(N_CHAIN, H_CHAIN), si.spectrum(N_CHAIN),
-                       si.sign(N_CHAIN))
-            Xs = si.vectors(1024, N_CHAIN, seed=123)
-            fns[nm] = lambda c, m=mode, U=U, d=d, s=s, Xs=Xs: oracle.apply(
-                m, U, np.resize(Xs, (c, N_CHAIN)), sign=s, d=d)
+        if nm.startswith("chain_") or nm.startswith("c2_"):
+            if nm.startswith("chain_"):
+                n, h, mode = N_CHAIN, H_CHAIN, nm.split("_")[1]
+            else:
+                n, h, _, mode = c2_shape(nm)
+            U, d, s = si.reflectors(n, h), si.spectrum(n), si.sign(n)
+            Xs = si.vectors(1024, n, seed=123)
+            fns[nm] = lambda c, m=mode, U=U, d=d, s=s, Xs=Xs, n=n: oracle.apply(
+                m, U, np.resize(Xs, (c, n)), sign=s, d=d)
         elif nm.startswith("wy_h"):
             h = int(nm[4:])
             U = si.reflectors(N_CHAIN, h, seed=h)
@@ -687,6 +886,14 @@ def oracle_units(names):
                     if ki > 0:
                         oracle.apply("W", U, np.resize(P, (ki, P.shape[1])))
             fns[nm] = f
+        elif nm == "trunc_qr":
+            from oracle import factor as OF
+
+            R, d, _, _ = OF.result3(si.random_orthonormal(N_TRQ, 31), H_TRQ)
+            Rr = R[::-1].copy()
+            Xs = si.vectors(256, N_TRQ, seed=127)
+            fns[nm] = lambda c, Rr=Rr, d=d, Xs=Xs: oracle.apply(
+                "WT", Rr, np.resize(Xs, (c, N_TRQ)), sign=d.astype(np.int8))
         elif nm == "adjoint_SYM":
             U, d = si.reflectors(N_ADJ, H_ADJ, seed=9), si.spectrum(N_ADJ, seed=9)
             Xs, Gs = si.vectors(256, N_ADJ, seed=125), si.vectors(256, N_ADJ, seed=126)
@@ -721,10 +928,12 @@ def oracle_rates(names, budget_s):
 
 
 def step_vectors(names):
-    per = {"chain": B_CHAIN, "wy": B_WY, "mahalanobis": P_MAHAL, "adjoint": B_ADJ}
+    per = {"chain": B_CHAIN, "wy": B_WY, "mahalanobis": P_MAHAL, "adjoint": B_ADJ,
+           "trunc": B_TRQ}
     if "batched_C5" in names:
         per["batched"] = sum(b for _, _, b, _ in c5_specs())
-    return {nm: per[nm.split("_")[0]] for nm in names}
+    return {nm: c2_shape(nm)[2] if nm.startswith("c2_") else per[nm.split("_")[0]]
+            for nm in names}
 
 
 def run_reference(args, names):
@@ -751,7 +960,10 @@ def run_reference(args, names):
     value = sum(full.values()) / step_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * step_s,
+            "ms_per_step_kind": "extrapolated: each row's per-unit time on its bounded sample "
+                                "times the row's full batch",
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian vectors, reflectors and mixture)",
             "config": config_dict(names),
@@ -783,9 +995,18 @@ def main():
     ap.add_argument("--tune-table", default=None,
                     help="batched launch: load tile shapes from this file if it exists, "
                          "else tune and save them there")
+    ap.add_argument("--ingest-traffic", default=None, metavar="CSV",
+                    help="record in --traffic-out the DRAM bytes of an ncu log whose launch i "
+                         "is the first launch of the i-th of --rows, and exit (no GPU)")
+    ap.add_argument("--traffic-out", default=TRAFFIC_JSON)
+    ap.add_argument("--traffic-command", default="",
+                    help="the ncu command line that wrote the log")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     names = [r for r in args.rows.split(",") if r]
+    if args.ingest_traffic:
+        ingest_traffic(args.ingest_traffic, names, args.traffic_out, args.traffic_command)
+        return 0
     global TUNE_TABLE
     TUNE_TABLE = args.tune_table
     if args.batch_scale != 1.0:
@@ -812,10 +1033,11 @@ def main():
     rows = make_rows(torch, dev, names)
     stream = torch.cuda.current_stream()
 
+    parity = {}
     for r in rows:  # first call and parity on sampled outputs, outside the timed region
         r.run()
-    torch.cuda.synchronize()
-    parity = {r.name: r.parity() for r in rows}
+        torch.cuda.synchronize()
+        parity[r.name] = r.parity()
     for _ in range(args.warmup):
         for r in rows:
             r.run()
@@ -871,15 +1093,20 @@ def main():
         s = ms / 1e3
         gbs, tfl = r.bytes() / s / 1e9, r.flops() / s / 1e12
         ach = gbs if r.bound == "hbm" else tfl
-        traffic = None
-        if isinstance(r, ChainRow):
-            traffic = profiled_traffic(r.mode, r.vectors())
-        elif isinstance(r, BatchedRow):
-            traffic = profiled_traffic("C5", r.vectors(), BATCHED_SOURCES, BATCHED_TRAFFIC_FILE)
+        traffic = profiled_traffic(r.name, r.vectors())
         out_rows[r.name] = {"ms": ms, "vectors_per_s": r.vectors() / s, "GB_s": gbs,
                             "TFLOP_s": tfl, "bound": r.bound, "frac": ach / peak_of[r.bound],
                             "hbm_frac": gbs / peaks["hbm_gbs"], "launches": r.launches,
                             "rel_l2_vs_oracle": parity[r.name], "dram_traffic_bytes": traffic}
+    c2_rows = [r for r in rows if r.name.startswith("c2_")]
+    c2 = None
+    if c2_rows:
+        c2_ms = sum(out_rows[r.name]["ms"] for r in c2_rows)
+        c2 = {"rows": [r.name for r in c2_rows], "ms": c2_ms,
+              "vectors_per_s": sum(r.vectors() for r in c2_rows) / (c2_ms / 1e3),
+              "GB_s": sum(r.bytes() for r in c2_rows) / (c2_ms / 1e3) / 1e9,
+              "min_frac": min(out_rows[r.name]["frac"] for r in c2_rows),
+              "max_rel_l2_vs_oracle": max(out_rows[r.name]["rel_l2_vs_oracle"] for r in c2_rows)}
     dom = max(rows, key=lambda r: out_rows[r.name]["ms"])
     d = out_rows[dom.name]
     psource = {"hbm": f"hbm_gbs {psrc}",
@@ -901,6 +1128,10 @@ def main():
     compare = None
     if not args.no_compare and any(isinstance(r, WYRow) for r in rows):
         compare = compare_fp32(torch, dev, [r for r in rows if isinstance(r, WYRow)], out_rows)
+    trunc_vs = None
+    for r in rows:
+        if isinstance(r, TruncRow) and not args.no_compare:
+            trunc_vs = r.compare()
     batched_vs = None
     for r in rows:
         if isinstance(r, BatchedRow):
@@ -931,8 +1162,8 @@ def main():
                 "data": "synthetic (seeded Gaussian vectors, reflectors and mixture)",
                 "config": config_dict(names), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * sum(r.launches for r in rows), "clocks": clocks,
-                "rows": out_rows, "bf16_wy_vs_fp32_chain": compare,
-                "batched_vs_separate": batched_vs,
+                "rows": out_rows, "c2": c2, "bf16_wy_vs_fp32_chain": compare,
+                "batched_vs_separate": batched_vs, "trunc_qr_skip_vs_dense": trunc_vs,
                 "fp32_peak_tflops": fp32_peak}
         print(json.dumps(line))
     if pg:
@@ -983,13 +1214,17 @@ def measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step, steps=5, warm
     parts = [r.e2e(torch) for r in rows]
     h2d = sum(p[0] for p in parts)
     d2h = sum(p[1] for p in parts)
-    chunks = [c for p in parts for c in p[2]]
+    # a chunk is (copy in, compute, copy out[, key]): its compute waits for the
+    # last copy out of the same key (by default the same chunk in the previous
+    # step), i.e. for the output buffers it is about to overwrite
+    chunks = [c if len(c) == 4 else tuple(c) + (("chunk", i),)
+              for i, c in enumerate(c for p in parts for c in p[2])]
     s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     last_comp = [None] * len(chunks)
-    last_out = [None] * len(chunks)
+    last_out = {}
 
     def step():
-        for i, (cin, comp, cout) in enumerate(chunks):
+        for i, (cin, comp, cout, key) in enumerate(chunks):
             with torch.cuda.stream(s_in):
                 if last_comp[i] is not None:
                     s_in.wait_event(last_comp[i])
@@ -998,16 +1233,16 @@ def measure_e2e(torch, rows, stream, world, pg, dev, vec_per_step, steps=5, warm
                 e_in.record(s_in)
             with torch.cuda.stream(s_comp):
                 s_comp.wait_event(e_in)
-                if last_out[i] is not None:
-                    s_comp.wait_event(last_out[i])
+                if key in last_out:
+                    s_comp.wait_event(last_out[key])
                 comp()
                 last_comp[i] = torch.cuda.Event()
                 last_comp[i].record(s_comp)
             with torch.cuda.stream(s_out):
                 s_out.wait_event(last_comp[i])
                 cout()
-                last_out[i] = torch.cuda.Event()
-                last_out[i].record(s_out)
+                last_out[key] = torch.cuda.Event()
+                last_out[key].record(s_out)
 
     for _ in range(warm):  # first touches of the pinned buffers are not timed
         step()

@@ -587,6 +587,10 @@ void wy_release_workspace(Plan *p) {
     w->V64 = w->G = w->T = nullptr;
 }
 
+#ifndef HH_WY_GRID_CAP
+#define HH_WY_GRID_CAP 0
+#endif
+
 hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void *Y, int64_t ldy,
                    int64_t batch, cudaStream_t st) {
     const WYPlan *w = reinterpret_cast<const WYPlan *>(p->wy);
@@ -605,7 +609,10 @@ hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void
     if (ea) return cuda_fail(ea, "compact-WY shared-memory opt-in");
     const int64_t tiles = (batch + wy::kTileM - 1) / wy::kTileM;
     if (tiles * wy::kTileM > 0x7fffffffLL) return fail(HH_ERR_INVALID_ARG, "batch too large");
-    const int grid = (int)std::min<int64_t>(tiles, p->num_sms > 0 ? p->num_sms : 1);
+    int grid = (int)std::min<int64_t>(tiles, p->num_sms > 0 ? p->num_sms : 1);
+#if HH_WY_GRID_CAP > 0
+    if (w->PB <= 64 && grid > HH_WY_GRID_CAP) grid = HH_WY_GRID_CAP;
+#endif
     // shared memory: as many epilogue boxes (up to 4) as leave room for at
     // least three operand stages, then the operand ring
     const size_t stage_bytes = 128 * 128 + (size_t)w->PB * 128;

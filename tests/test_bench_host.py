@@ -1,14 +1,13 @@
 """Host-side logic of bench.py (no GPU).
 
-* The traffic figure of the roofline object comes from a committed ncu summary
-  only while the kernel sources hash to the value recorded beside it.
-* The committed summaries carry parseable per-vector traffic lines.
+* The traffic figure of a row comes from profiles/traffic.json only while the
+  row's kernel sources hash to the value recorded with it; ncu CSV logs are
+  read in bytes whatever unit ncu printed.
 * The pipelined end-to-end step's row chunks cover each batch exactly once.
 * The reference arm (the FP64 oracle on the host cores) prints one JSON line
   with the contract's keys.
 """
 
-import hashlib
 import json
 import os
 import re
@@ -23,37 +22,62 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def _sha(files):
-    h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+NCU_CSV = """==PROF== Connected to process 1
+"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"
+"0","1","python","h","k","1","7","(256, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_read.sum","Gbyte","4.30"
+"0","1","python","h","k","1","7","(256, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_write.sum","Mbyte","4,290.5"
+"1","1","python","h","k","1","7","(256, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_read.sum","Gbyte","9.00"
+"""
 
 
-def test_profiled_traffic_lookup(tmp_path):
-    sha = _sha(bench.KERNEL_SOURCES)
-    p = tmp_path / "summary.md"
-    p.write_text("text\n"
-                 f"TRAFFIC mode=W bytes_per_vector=100.5 sources_sha256={sha}\n"
-                 "TRAFFIC mode=WT bytes_per_vector=7 sources_sha256=0000000000000000\n")
-    assert bench.profiled_traffic("W", 10, path=str(p)) == pytest.approx(1005.0)
-    assert bench.profiled_traffic("WT", 10, path=str(p)) is None      # stale capture
-    assert bench.profiled_traffic("SYM", 10, path=str(p)) is None     # no line for the mode
-    assert bench.profiled_traffic("W", 10, path=str(tmp_path / "absent.md")) is None
+def test_ncu_csv_launches_in_bytes(tmp_path):
+    p = tmp_path / "log.csv"
+    p.write_text(NCU_CSV.replace('"9.00"\n', '"9.00"\n"1","1","python","h","k","1","7","x","y","0",'
+                                             '"10.3","s","dram__bytes_write.sum","byte","12"\n'))
+    got = bench.ncu_dram_bytes(str(p))
+    assert got[0] == (pytest.approx(4.30e9), pytest.approx(4290.5e6))
+    assert got[1] == (pytest.approx(9.0e9), pytest.approx(12.0))
 
 
-@pytest.mark.parametrize("path,modes", [(bench.TRAFFIC_FILE, ("W", "WT", "SYM")),
-                                        (bench.BATCHED_TRAFFIC_FILE, ("C5",))])
-def test_committed_traffic_lines_parse(path, modes):
-    lines = [ln for ln in open(path) if ln.startswith("TRAFFIC ")]
-    seen = set()
-    for ln in lines:
-        kv = dict(t.split("=", 1) for t in ln.split()[1:])
-        assert float(kv["bytes_per_vector"]) > 0
-        assert re.fullmatch(r"[0-9a-f]{16}", kv["sources_sha256"])
-        seen.add(kv["mode"])
-    assert set(modes) <= seen
+def test_traffic_ingest_and_lookup(tmp_path):
+    p = tmp_path / "log.csv"
+    p.write_text(NCU_CSV.replace('"9.00"\n', '"9.00"\n"1","1","python","h","k","1","7","x","y","0",'
+                                             '"10.3","s","dram__bytes_write.sum","byte","12"\n'))
+    out = tmp_path / "traffic.json"
+    bench.ingest_traffic(str(p), ["chain_W", "c2_n1024_h10_SYM"], str(out), "ncu ... bench.py")
+    data = json.loads(out.read_text())
+    rows = {e["row"]: e for e in data["entries"]}
+    assert rows["chain_W"]["units"] == bench.B_CHAIN
+    assert rows["c2_n1024_h10_SYM"]["units"] == 1_048_576
+    assert rows["c2_n1024_h10_SYM"]["dram_read_bytes"] == pytest.approx(9.0e9)
+    full = 4.30e9 + 4290.5e6
+    assert bench.profiled_traffic("chain_W", bench.B_CHAIN, str(out)) == pytest.approx(full)
+    assert bench.profiled_traffic("chain_W", bench.B_CHAIN // 2, str(out)) == pytest.approx(full / 2)
+    assert bench.profiled_traffic("chain_WT", 10, str(out)) is None       # no figure
+    with pytest.raises(ValueError):                                       # too few launches
+        bench.ingest_traffic(str(p), ["chain_W", "chain_WT", "chain_SYM"], str(out), "")
+    # a figure recorded against other kernel sources is not used
+    rows["chain_W"]["sources_sha256"] = "0000000000000000"
+    out.write_text(json.dumps({"entries": list(rows.values())}))
+    assert bench.profiled_traffic("chain_W", bench.B_CHAIN, str(out)) is None
+    assert bench.profiled_traffic("chain_W", 1, str(tmp_path / "absent.json")) is None
+
+
+def test_committed_traffic_file_parses():
+    if not os.path.exists(bench.TRAFFIC_JSON):
+        pytest.skip("no traffic figures recorded")
+    data = json.load(open(bench.TRAFFIC_JSON))
+    for e in data["entries"]:
+        assert e["row"] in bench.ALL_ROWS
+        assert e["dram_read_bytes"] > 0 and e["dram_write_bytes"] > 0 and e["units"] > 0
+        assert re.fullmatch(r"[0-9a-f]{16}", e["sources_sha256"])
+        assert "ncu" in e["command"] and "--clock-control none" in e["command"]
+
+
+def test_c2_rows_have_shapes():
+    for nm in bench.C2_ROWS:
+        n, h, b, mode = bench.c2_shape(nm)
+        assert mode in ("W", "WT", "SYM") and b in (1_048_576, 262_144)
 
 
 @pytest.mark.parametrize("B", [1, 7, 16, 17, 1000, 262144])

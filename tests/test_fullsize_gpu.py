@@ -7,10 +7,15 @@ checks properties that hold at any size on every output:
     262,144 vectors with h = 12, 16 and 64; modes W, W^T, S): sampled rows within
     1e-5 relative L2, every row finite, |W x| = |x| per row for W and W^T;
   * BF16 compact-WY (n = 4096, 262,144 vectors, h = 64 / 256 / 1024): sampled
-    rows within 1e-2 of the oracle on the BF16-rounded data, norms kept to 1e-2;
-  * adjoint of S (n = 1024, h = 32, 65,536 vectors): sampled rows of dL/dX
-    against the oracle; dL/dv and dL/dd add up over two halves of the batch;
+    rows within 1e-2 of the oracle both on the BF16-rounded data (the kernel's
+    arithmetic) and on the unrounded FP32 reflectors and vectors (end to end),
+    norms kept to 1e-2;
+  * adjoint of S (n = 1024, h = 32, 65,536 vectors): dL/dv and dL/dd of the whole
+    batch against the oracle's (FP64, states stored), sampled rows of dL/dX, and
+    the sums over two halves of the batch;
   * fast Mahalanobis distance (n = 256, h = 16, 1,048,576 pairs): sampled pairs;
+    its gradient over all pairs against the oracle's composition (the W^T
+    adjoint seeded with 2 g d .* z, and sum g z .* z for d);
   * batched launch, 512 ragged transforms: every transform on 64 vectors.
 """
 
@@ -77,18 +82,28 @@ def test_bf16_wy_full_size(h):
     from paper_1811_07624_gb300 import Plan
 
     n, batch = 4096, 262144
-    Ub = torch.tensor(si.reflectors(n, h, seed=h), dtype=torch.float32).bfloat16()
+    U32 = torch.tensor(si.reflectors(n, h, seed=h), dtype=torch.float32)
+    Ub = U32.bfloat16()
     plan = Plan(Ub.to(DEV))
-    X = _gaussian(batch, n, seed=h + 1, dtype=torch.bfloat16)
+    X32 = _gaussian(batch, n, seed=h + 1)
+    X = X32.bfloat16()
     idx = _sample(batch, 48)
     Xs = X[idx].double().cpu().numpy()
+    X32s = X32[idx].double().cpu().numpy()
+    del X32
     for mode in ("W", "WT"):
         Y = plan.apply_mode(mode, X)
         plan.sync()
         assert bool(torch.isfinite(Y).all())
+        Ys = Y[idx].double().cpu().numpy()
+        # (ii) the kernel's arithmetic: oracle on the BF16-rounded reflectors and vectors
         ref = oracle.apply(mode, Ub.double().numpy(), Xs)
-        err = _rel(Y[idx].double().cpu().numpy(), ref)
+        err = _rel(Ys, ref)
         assert err <= 1e-2, f"{mode} h={h}: {err:.2e}"
+        # (i) end to end: oracle on the unrounded FP32 reflectors and vectors
+        ref32 = oracle.apply(mode, U32.double().numpy(), X32s)
+        err32 = _rel(Ys, ref32)
+        assert err32 <= 1e-2, f"{mode} h={h} (unrounded inputs): {err32:.2e}"
         ratio = Y.float().norm(dim=1) / X.float().norm(dim=1)
         assert float((ratio - 1).abs().max()) <= 1e-2
         del Y
@@ -115,6 +130,18 @@ def test_adjoint_sym_full_size():
     rX, _, _ = oracle.backward("SYM", U32.double().numpy(), X[idx].double().cpu().numpy(),
                                G[idx].double().cpu().numpy(), d=d32.double().numpy())
     assert _rel(gX[idx].double().cpu().numpy(), rX) <= 1e-4
+    # the whole batch's dL/dv and dL/dd against the oracle (in row chunks; the
+    # gradients are sums over rows)
+    rU = np.zeros((h, n))
+    rd = np.zeros(n)
+    for r0 in range(0, batch, 8192):
+        _, cU, cd = oracle.backward("SYM", U32.double().numpy(),
+                                    X[r0:r0 + 8192].double().cpu().numpy(),
+                                    G[r0:r0 + 8192].double().cpu().numpy(), d=d32.double().numpy())
+        rU += cU
+        rd += cd
+    assert _rel(gU.double().cpu().numpy(), rU) <= 1e-4
+    assert _rel(gd.double().cpu().numpy(), rd) <= 1e-4
     plan.close()
 
 
@@ -166,3 +193,35 @@ def test_batched_512_transforms_full_size():
     assert worst <= 1e-5, f"worst transform: {worst:.2e}"
     for p in plans:
         p.close()
+
+
+def test_mahalanobis_grad_full_size():
+    from paper_1811_07624_gb300 import Plan
+
+    n, h, npairs = 256, 16, 1 << 20
+    Xp, labels = si.gaussian_mixture(100_000, n=n, seed=0)
+    ia, ib, _ = si.labelled_pairs(labels, npairs, seed=0)
+    U32 = torch.tensor(si.reflectors(n, h, seed=7), dtype=torch.float32)
+    d32 = torch.tensor(si.spectrum(n, seed=7), dtype=torch.float32)
+    plan = Plan(U32.to(DEV), d=d32.to(DEV))
+    Xg = torch.tensor(Xp, dtype=torch.float32, device=DEV)
+    gout = torch.tensor(np.random.default_rng(3).uniform(-1, 1, npairs) / npairs,
+                        dtype=torch.float32, device=DEV)
+    gU, gd = plan.mahalanobis_backward(Xg, torch.tensor(ia, device=DEV), torch.tensor(ib, device=DEV),
+                                       gout)
+    plan.sync()
+    U64, d64 = U32.double().numpy(), d32.double().numpy()
+    X64 = Xg.double().cpu().numpy()
+    g64 = gout.double().cpu().numpy()
+    rU = np.zeros((h, n))
+    rd = np.zeros(n)
+    for p0 in range(0, npairs, 1 << 17):
+        sl = slice(p0, p0 + (1 << 17))
+        delta = X64[ia[sl]] - X64[ib[sl]]
+        z = oracle.apply("WT", U64, delta)
+        _, cU, _ = oracle.backward("WT", U64, delta, 2.0 * g64[sl, None] * d64[None, :] * z)
+        rU += cU
+        rd += (g64[sl, None] * z * z).sum(0)
+    assert _rel(gU.double().cpu().numpy(), rU) <= 1e-4
+    assert _rel(gd.double().cpu().numpy(), rd) <= 1e-4
+    plan.close()
