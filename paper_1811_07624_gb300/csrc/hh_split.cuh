@@ -1,4 +1,6 @@
-// Column-split F32 reflector-chain kernel on two-CTA clusters.
+// Column-split F32 reflector-chain kernel on clusters of CL CTAs (two in the
+// configuration the library dispatches; CL = 1 keeps all of V in one CTA and
+// needs no exchange when a row group is one warp).
 //
 // The arithmetic is the staged kernel's: the chain of §II-A (Eq. (1)-(2)),
 // B consecutive reflectors per round, with the dot products of a round taken
@@ -155,22 +157,23 @@ __device__ __forceinline__ void scale_half(float2 (&x)[RT][XCfg<G, NG, RT, RG, B
 
 // Per-row-group exchange state: the round counter selects the receive buffer
 // (round & 1) and the phase parity of its mbarrier ((round >> 1) & 1).
+template <int CL>
 struct Exchange {
     uint32_t round;
-    uint32_t rank;       // this CTA's rank in the cluster
-    uint32_t peer_slot;  // the peer CTA's receive slots of this row group (shared::cluster)
-    uint32_t peer_bar;   // the peer CTA's receive mbarriers of this row group
-    bool waiting;        // false once a wait of this thread expired
+    uint32_t rank;               // this CTA's rank in the cluster
+    uint32_t peer_slot[CL > 1 ? CL - 1 : 1];  // the other CTAs' receive slots (shared::cluster)
+    uint32_t peer_bar[CL > 1 ? CL - 1 : 1];   // ... and their receive mbarriers
+    bool waiting;                // false once a wait of this thread expired
 };
 
 // Apply h reflectors, ascending (k = 0..h-1) or descending, to the RT rows in
 // x, B per round.  vs holds this CTA's half of every reflector (row k at
 // vs + k*HALF).
-template <int G, int NG, int RT, int RG, int B>
+template <int G, int NG, int RT, int RG, int B, int CL>
 __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2], bool asc, int h,
                                       const float *vs, const float *__restrict__ tau,
                                       const float *__restrict__ gram, int t, int lane, int warp,
-                                      float *slot, uint64_t *bars, Exchange &xc, int *err) {
+                                      float *slot, uint64_t *bars, Exchange<CL> &xc, int *err) {
     using C = XCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L, HALF = C::HALF;
     (void)NW;
@@ -219,33 +222,43 @@ __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2
         float q = fused::warp_reduce_rows<float, NV>(p, lane);  // lane holds value lane / L
         const int idx = lane / L, sub = lane & (L - 1);
         // q: this warp's part of value idx, held by the L lanes of idx.  Every
-        // warp posts its part into slot [b][rank][warp][idx] of both CTAs: its
-        // own with a shared store and an arrival, the peer's with st.async,
-        // which completes bytes on the peer's mbarrier.  Once a CTA's barrier
-        // phase completes it holds all 2*NW parts, and both CTAs add them in
-        // the same fixed order.
-        const uint32_t b = xc.round & 1u, par = (xc.round >> 1) & 1u;
-        if (sub == 0) {
-            const uint32_t off = ((b * 2u + xc.rank) * NW + warp) * NV + idx;
-            slot[off] = q;
-            st_async_f32(xc.peer_slot + off * 4u, q, xc.peer_bar + b * 8u);
-        }
-        __syncwarp();
-        if (lane == 0) {
-            if (warp == 0)
-                mbar_arrive_expect_tx(bars + b, NW * NV * 4u);  // + the peer's parts
-            else
-                mbar_arrive(bars + b);
-        }
-        if (xc.waiting && !wait_cluster_bounded(bars + b, par)) {
-            atomicExch(err, (int)HH_ERR_TIMEOUT);
-            xc.waiting = false;
-        }
-        float zz = 0.f;
+        // warp posts its part into slot [b][rank][warp][idx] of every CTA of
+        // the cluster: its own with a shared store and an arrival, the others'
+        // with st.async, which completes bytes on their mbarriers.  Once a
+        // CTA's barrier phase completes it holds all CL*NW parts, and every
+        // CTA adds them in the same fixed order.
+        float zz;
+        if constexpr (CL == 1 && NW == 1) {
+            zz = q;  // one warp holds all columns: the shuffle reduction is the whole sum
+            (void)slot;
+            (void)bars;
+            (void)err;
+        } else {
+            const uint32_t b = xc.round & 1u, par = (xc.round >> 1) & 1u;
+            if (sub == 0) {
+                const uint32_t off = ((b * CL + xc.rank) * NW + warp) * NV + idx;
+                slot[off] = q;
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+                for (int pc = 0; pc < CL - 1; ++pc)
+                    st_async_f32(xc.peer_slot[pc] + off * 4u, q, xc.peer_bar[pc] + b * 8u);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                if (warp == 0)
+                    mbar_arrive_expect_tx(bars + b, (CL - 1) * NW * NV * 4u);  // + the others' parts
+                else
+                    mbar_arrive(bars + b);
+            }
+            if (xc.waiting && !wait_cluster_bounded(bars + b, par)) {
+                atomicExch(err, (int)HH_ERR_TIMEOUT);
+                xc.waiting = false;
+            }
+            zz = 0.f;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) zz += slot[((b * 2u + c) * NW + w) * NV + idx];
+            for (int c = 0; c < CL; ++c)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) zz += slot[((b * CL + c) * NW + w) * NV + idx];
+        }
         ++xc.round;
         float z[NV];
 #pragma unroll
@@ -284,8 +297,8 @@ __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2
 // Y rows and bases 16-byte aligned, V rows zero padded to ldv >= 2*HALF,
 // ldv % 4 == 0, h*HALF floats of dynamic shared memory.  Launched as clusters
 // of two CTAs (cluster rank = the half of the columns a CTA owns).
-template <int MODE, int G, int NG, int RT, int RG, int B>
-__global__ void __launch_bounds__(G *RG, 1)
+template <int MODE, int G, int NG, int RT, int RG, int B, int CL, int MINB>
+__global__ void __launch_bounds__(G *RG, MINB)
 split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t batch, int n,
                    const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv, int h,
                    const float *__restrict__ gram, const float *__restrict__ sign,
@@ -297,7 +310,7 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
     // per row group, two buffers of 2 CTAs x NW warps x NV partial dot products,
     // each completed on its own mbarrier (NW local arrivals + the peer's bytes)
     __shared__ __align__(8) uint64_t rbar[RG][2];
-    __shared__ __align__(16) float rslot[RG][2 * 2 * C::NW * NV];
+    __shared__ __align__(16) float rslot[RG][2 * CL * C::NW * NV];
 
     const int tid = threadIdx.x;
     const int rg = tid / G;
@@ -324,11 +337,15 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
     }
     // every mbarrier of the cluster is initialised before any peer stores into it
     cluster_sync();
-    Exchange xc;
+    Exchange<CL> xc;
     xc.round = 0;
     xc.rank = rank;
-    xc.peer_slot = peer_addr(smem_u32(&rslot[rg][0]), rank ^ 1u);
-    xc.peer_bar = peer_addr(smem_u32(&rbar[rg][0]), rank ^ 1u);
+#pragma unroll
+    for (int pc = 0; pc < CL - 1; ++pc) {
+        const uint32_t other = (rank + 1u + (uint32_t)pc) % (uint32_t)CL;
+        xc.peer_slot[pc] = peer_addr(smem_u32(&rslot[rg][0]), other);
+        xc.peer_bar[pc] = peer_addr(smem_u32(&rbar[rg][0]), other);
+    }
     xc.waiting = true;
     if (h > 0 && !wait_cluster_bounded(&vbar, 0)) {
         atomicExch(err, (int)HH_ERR_TIMEOUT);
@@ -344,7 +361,8 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
             const int64_t nr0 = (tl + ncl * RG) * RT;
 #pragma unroll
             for (int r = 0; r < RT; ++r)
-                if (nr0 + r < batch) prefetch_l2(X + (nr0 + r) * ldx + c0, (uint32_t)ncols * 4u);
+                if (ncols > 0 && nr0 + r < batch)
+                    prefetch_l2(X + (nr0 + r) * ldx + c0, (uint32_t)ncols * 4u);
         }
         float2 x[RT][E2];
 #pragma unroll
@@ -365,8 +383,8 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
         for (int half = 0; half < (MODE == HH_MODE_SYM ? 2 : 1); ++half) {
             if (half == 1) scale_half<G, NG, RT, RG, B>(x, d, c0, t);
             const bool asc = MODE != HH_MODE_W && half == 0;
-            chain<G, NG, RT, RG, B>(x, asc, h, vs, tau, gram, t, lane, warp, &rslot[rg][0],
-                                    &rbar[rg][0], xc, err);
+            chain<G, NG, RT, RG, B, CL>(x, asc, h, vs, tau, gram, t, lane, warp, &rslot[rg][0],
+                                        &rbar[rg][0], xc, err);
         }
         if (MODE != HH_MODE_WT && sign) scale_half<G, NG, RT, RG, B>(x, sign, c0, t);
 #pragma unroll
@@ -388,22 +406,29 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
     cluster_sync();
 }
 
-// Largest dynamic shared memory a launch may request (h*HALF floats).
-constexpr size_t kMaxSmem = 200 * 1024;
-
-template <int G, int NG, int RT, int RG, int B>
-constexpr int max_h() {
-    return (int)(kMaxSmem / (XCfg<G, NG, RT, RG, B>::HALF * sizeof(float)));
+// Largest dynamic shared memory a launch may request (h*HALF floats): one CTA
+// per SM may take 200 KiB, two take 100 KiB each.
+template <int MINB>
+constexpr size_t max_smem() {
+    return MINB >= 2 ? 100 * 1024 : 200 * 1024;
 }
 
-template <int G, int NG, int RT, int RG, int B>
+template <int G, int NG, int RT, int RG, int B, int MINB = 1>
+constexpr int max_h() {
+    return (int)(max_smem<MINB>() / (XCfg<G, NG, RT, RG, B>::HALF * sizeof(float)));
+}
+
+// CL CTAs per cluster split the columns (CTA r owns [r*HALF, (r+1)*HALF));
+// MINB CTAs per SM bound the registers.
+template <int G, int NG, int RT, int RG, int B, int CL = 2, int MINB = 1>
 cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                    int64_t batch, int n, const float *V, const float *tau, int64_t ldv, int h,
                    const float *gram, const float *sign, const float *d, int *err,
                    cudaStream_t st) {
     using C = XCfg<G, NG, RT, RG, B>;
-    if (n <= C::HALF || n > 2 * C::HALF || n % 4 || ldv < 2 * C::HALF || ldv % 4 ||
-        h > max_h<G, NG, RT, RG, B>())
+    constexpr size_t kMaxSmem = max_smem<MINB>();
+    if (n < 1 || n > CL * C::HALF || n % 4 || ldv < CL * C::HALF || ldv % 4 ||
+        h > max_h<G, NG, RT, RG, B, MINB>())
         return cudaErrorInvalidValue;
     const size_t smem = h > 0 ? (size_t)h * C::HALF * sizeof(float) : 16;
     // per kernel (one per mode) and device: the shared-memory opt-in at the
@@ -413,7 +438,7 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.x = CL;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.blockDim = dim3(C::THREADS);
@@ -426,7 +451,7 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
                                                   (int)kMaxSmem);
             if (e2 != cudaSuccess) return e2;
             cudaLaunchConfig_t q = cfg;
-            q.gridDim = dim3(2);
+            q.gridDim = dim3(CL);
             q.dynamicSmemBytes = kMaxSmem;
             int nc = 0;
             e2 = cudaOccupancyMaxActiveClusters(&nc, kern, &q);
@@ -437,15 +462,15 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
         if (e != cudaSuccess) return e;
         const int64_t groups = ((batch + RT - 1) / RT + RG - 1) / RG;  // row-group tiles / RG
         const int grid_cl = (int)(groups < ncl ? groups : ncl);
-        cfg.gridDim = dim3(2 * grid_cl);
+        cfg.gridDim = dim3(CL * grid_cl);
         cfg.dynamicSmemBytes = smem;
         return cudaLaunchKernelEx(&cfg, kern, X, ldx, Y, ldy, batch, n, V, tau, ldv, h, gram,
                                   sign, d, err);
     };
     switch (mode) {
-        case HH_MODE_W: return run(split_chain_kernel<HH_MODE_W, G, NG, RT, RG, B>);
-        case HH_MODE_WT: return run(split_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B>);
-        default: return run(split_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B>);
+        case HH_MODE_W: return run(split_chain_kernel<HH_MODE_W, G, NG, RT, RG, B, CL, MINB>);
+        case HH_MODE_WT: return run(split_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B, CL, MINB>);
+        default: return run(split_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B, CL, MINB>);
     }
 }
 
