@@ -30,6 +30,8 @@
 
 // Column-split cluster kernel for 2048 < n <= 4096 (each CTA of a pair keeps
 // its 2048 columns of every reflector in shared memory): (G, NG, RT, RG, B).
+// For 512 < n <= 1024 the same kernel runs on single-CTA "clusters" holding
+// all of V (configurations in the dispatch below).
 #ifndef HH_SPLIT_G
 #define HH_SPLIT_G 64
 #define HH_SPLIT_NG 8
@@ -58,6 +60,19 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
         if (n <= 128) return HH_STAGED(32, 1, 8, 4, 2);
         if (n <= 256) return HH_STAGED(32, 2, 8, 4, 2);
         if (n <= 512) return HH_STAGED(32, 4, 4, 4, 2);
+#ifndef HH_NO_SPLIT
+        // 512 < n <= 1024 with h <= 50: every reflector resident in one CTA's
+        // shared memory, one warp per row group (no exchange); four reflectors
+        // per round from h = 16, two below (measured).
+        if (n > 512 && n <= 1024 && !start && h >= 1 &&
+            h <= split::max_h<32, 8, 4, 8, 4, 1>()) {
+            if (h >= 16)
+                return split::launch<32, 8, 4, 8, 4, 1, 1>(mode, X, ldx, Y, ldy, batch, ni, U, tau,
+                                                           ldv, h, gram, sign, d, err, st);
+            return split::launch<32, 8, 4, 8, 2, 1, 1>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv,
+                                                       h, gram, sign, d, err, st);
+        }
+#endif
         if (n <= 1024) return HH_STAGED(HH_N1024_G, HH_N1024_NG, HH_N1024_RT, HH_N1024_RG, HH_N1024_B);
         if (n <= 2048) return HH_STAGED(HH_N2048_G, HH_N2048_NG, HH_N2048_RT, HH_N2048_RG, HH_N2048_B);
 #ifndef HH_NO_SPLIT

@@ -168,6 +168,32 @@ def test_permutation_chain_exact_large():
     assert np.array_equal(got, y)
 
 
+@pytest.mark.parametrize("n", [516, 768, 1020, 1024])
+@pytest.mark.parametrize("h", [1, 15, 16, 50, 51])
+def test_resident_reflectors_single_cta(n, h):
+    """512 < n <= 1024, h <= 50: all reflectors resident in one CTA (two or four
+    reflectors per round either side of h = 16); h = 51 takes the staged kernel."""
+    for mode in ("W", "WT", "SYM"):
+        _check(mode, n, h, 37, torch.float32, seed=n + h)
+
+
+def test_permutation_chain_exact_resident():
+    # the same exactness through the single-CTA resident-reflector kernel (n = 1024)
+    rng = np.random.default_rng(4)
+    n, h, B = 1024, 20, 40
+    pairs = [tuple(rng.choice(n, 2, replace=False)) for _ in range(h)]
+    U = np.zeros((h, n))
+    for k, (i, j) in enumerate(pairs):
+        U[k, i], U[k, j] = 1.0, -1.0
+    x = rng.integers(-1000, 1000, size=(B, n)).astype(np.float64)
+    y = x.copy()
+    for (i, j) in reversed(pairs):
+        y[:, [i, j]] = y[:, [j, i]]
+    plan = _plan(U, dtype=torch.float32)
+    got = _as64(plan.apply(torch.as_tensor(x, dtype=torch.float32, device=DEV)))
+    assert np.array_equal(got, y)
+
+
 # --- properties -------------------------------------------------------------------
 
 def test_orthonormality_on_gpu():
