@@ -26,7 +26,9 @@ scale rows alone.
 Each row also reports its own time, vectors/s, algorithmic GB/s and FLOP/s
 and roofline fraction; the FP32 chain on the WY rows' shapes and data is
 timed beside them ("BF16-WY vs FP32 plain"), and the 512 transforms of
-batched_C5 are also timed as 512 separate launches ("batched_vs_separate").  `--impl reference` times the
+batched_C5 are also timed as 512 separate launches ("batched_vs_separate"), and
+"shf_su_fit" times SHF-SU's start and one iteration (n = 128, h = 16) through the
+kernels beside the FP64 oracle.  `--impl reference` times the
 FP64 CPU oracle on a bounded sample of the same rows.
 
     python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--gpus N]
@@ -630,6 +632,30 @@ class TruncRow:
         return Xh.numel() * 4, Yh.numel() * 4, chunks
 
 
+def fitting_compare(torch, dev, n=128, h=16, seed=0):
+    """SHF-SU (Algorithm 1) on a random symmetric n x n target: the start of step
+    2 and one outer iteration through the library's kernels, beside the FP64
+    oracle doing the same, with both runs' relative errors (Eq. (32))."""
+    import synthetic_inputs as si
+    from oracle import shf as O
+    from paper_1811_07624_gb300 import shf
+
+    S = si.random_symmetric(n, seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = shf.SHF(torch.tensor(S, device=dev), h)
+    st.iterate(spectrum_update=True, inner=20)
+    err_gpu = st.objective() / (4.0 * st.norm_S2)
+    torch.cuda.synchronize()
+    gpu_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref = O.shf(S, h, K=1, spectrum_update_=True, inner=20, tol=0.0)
+    cpu_s = time.perf_counter() - t0
+    return {"n": n, "h": h, "gpu_s": gpu_s, "oracle_s": cpu_s,
+            "relative_error_gpu": err_gpu, "relative_error_oracle": ref["relative_error"][-1],
+            "what": "SHF-SU start (step 2) and one outer iteration, inner <= 20 steps per reflector"}
+
+
 def c5_specs():
     """The 512 transforms: (n, h, batch, seed), batches scaled by --batch-scale."""
     import synthetic_inputs as si
@@ -1144,6 +1170,10 @@ def main():
                 batched_vs["speedup_vs_separate_graph"] = (batched_vs["separate_launches_graph_ms"]
                                                            / out_rows[r.name]["ms"])
 
+    fitting = None
+    if rank == 0 and not args.no_compare:
+        fitting = fitting_compare(torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rates, _ = oracle_rates(names, budget_s=2.0)
@@ -1164,6 +1194,7 @@ def main():
                 "gpu_launches": args.steps * sum(r.launches for r in rows), "clocks": clocks,
                 "rows": out_rows, "c2": c2, "bf16_wy_vs_fp32_chain": compare,
                 "batched_vs_separate": batched_vs, "trunc_qr_skip_vs_dense": trunc_vs,
+                "shf_su_fit": fitting,
                 "fp32_peak_tflops": fp32_peak}
         print(json.dumps(line))
     if pg:
