@@ -78,7 +78,8 @@ _CHAIN_SRC = [_CSRC + f for f in ("hh_split.cuh", "hh_staged.cuh", "hh_fused.cuh
 ROW_SOURCES = {
     "chain": _CHAIN_SRC, "c2": _CHAIN_SRC,
     "wy": [_CSRC + "hh_wy.cu", _CSRC + "hh_tc.cuh"],
-    "mahalanobis": [_CSRC + "hh_mahalanobis.cu", _CSRC + "hh_backward.cu", _CSRC + "hh_fused.cuh"],
+    "mahalanobis": [_CSRC + "hh_mahalanobis.cu", _CSRC + "hh_fused.cuh"],
+    "mahalanobis_grad": [_CSRC + "hh_backward.cu", _CSRC + "hh_fused.cuh"] + _CHAIN_SRC,
     "adjoint": [_CSRC + "hh_backward.cu", _CSRC + "hh_fused.cuh"] + _CHAIN_SRC,
     "batched": [_CSRC + "hh_batched.cu", _CSRC + "hh_staged.cuh", _CSRC + "hh_fused.cuh"],
     "trunc": _CHAIN_SRC,
@@ -109,7 +110,7 @@ def sources_sha(files):
 
 
 def row_kind(name):
-    return name.split("_")[0]
+    return name if name == "mahalanobis_grad" else name.split("_")[0]
 
 
 def profiled_traffic(row, units, path=None):
