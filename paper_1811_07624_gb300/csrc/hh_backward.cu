@@ -25,6 +25,7 @@
 // its partials to the scratch, and a second kernel sums the partials in a
 // fixed order in FP64 and forms dL/dv_k = tau_k P_k - tau_k^2 s_k v_k.
 #include <algorithm>
+#include <type_traits>
 
 #include "hh_fused.cuh"
 
@@ -199,6 +200,264 @@ __device__ __forceinline__ void backward_step(T (&a)[RT][BCfg<T, G, NG, RT>::E],
         for (int e = 0; e < VEC; ++e) pk[(size_t)(t + G * i) * VEC + e] += acc[i * VEC + e];
 }
 
+// Sum the NV per-thread values in p over the G threads of the CTA (any power
+// of two NV <= 32); every thread gets all NV sums.
+template <typename T, int G, int NV>
+__device__ __forceinline__ void cta_sum_n(T (&p)[NV], int lane, int warp, T *red, int &buf) {
+    constexpr int NW = G / 32, L = 32 / NV;
+    static_assert(NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two <= 32");
+    T v = fused::warp_reduce_rows<T, NV>(p, lane);
+    if constexpr (NW == 1) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) p[q] = __shfl_sync(0xffffffffu, v, q * L);
+    } else {
+        if ((lane & (L - 1)) == 0) red[fused::red_index<1, NV, NW>(buf, 0, lane / L, warp)] = v;
+        __syncthreads();
+        const int idx = lane / L, sub = lane & (L - 1);
+        T q = T(0);
+        for (int w = sub; w < NW; w += L) q += red[fused::red_index<1, NV, NW>(buf, 0, idx, w)];
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+#pragma unroll
+        for (int qq = 0; qq < NV; ++qq) p[qq] = __shfl_sync(0xffffffffu, q, qq * L);
+        buf ^= 1;
+    }
+}
+
+// BB backward reflector steps in one round (the Gram correction of the
+// blocked forward chain, run backwards).  With (a, g) the round's starting
+// state and k_0, k_1, ... the round's reflectors in walking order, the 2 BB
+// dot products v_{k_i} . a and v_{k_i} . g of every row are taken at the
+// start and reduced over the CTA together (one reduction per round instead
+// of one per reflector); the values each step needs follow from
+//     alpha_i = v_i . a - sum_{j<i} tau_j alpha_j (v_i . v_j)
+//     beta_i  = v_i . g - sum_{j<i} tau_j beta_j  (v_i . v_j)
+// (the Gram band v_k . v_{k+j}, j <= 15, of the plan).  The updates of a and
+// g and the P_k accumulations then run reflector by reflector per column.
+// k_i = k0 - i (DESC) or k0 + i.
+template <typename T, int G, int NG, int RT, int BB, bool DESC>
+__device__ __forceinline__ void backward_round(T (&a)[RT][BCfg<T, G, NG, RT>::E],
+                                               T (&g)[RT][BCfg<T, G, NG, RT>::E],
+                                               const T *__restrict__ V, int64_t ldv, int k0,
+                                               const T *__restrict__ tau,
+                                               const T *__restrict__ gram, T *accp, double *sacc,
+                                               int t, int lane, int warp, T *red, int &buf) {
+    using C = BCfg<T, G, NG, RT>;
+    constexpr int VEC = C::VEC, COVER = C::COVER;
+    constexpr int NVB = 2 * BB * RT;
+    static_assert(VEC % 2 == 0, "columns go in pairs");
+    auto kk = [&](int i) { return DESC ? k0 - i : k0 + i; };
+    T p[NVB];
+    {
+        T s0[NVB], s1[NVB];
+#pragma unroll
+        for (int q = 0; q < NVB; ++q) s0[q] = s1[q] = T(0);
+#pragma unroll
+        for (int ig = 0; ig < NG; ++ig) {
+            T vv[BB][VEC];
+#pragma unroll
+            for (int i = 0; i < BB; ++i)
+                fused::ldg_granule<T>(V + (size_t)kk(i) * ldv + (size_t)(t + G * ig) * VEC, vv[i]);
+#pragma unroll
+            for (int e = 0; e < VEC; e += 2) {
+                const int c = ig * VEC + e;
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int i = 0; i < BB; ++i) {
+                        fma_pair(s0[i * RT + r], s1[i * RT + r], a[r][c], a[r][c + 1], vv[i][e],
+                                 vv[i][e + 1]);
+                        fma_pair(s0[(BB + i) * RT + r], s1[(BB + i) * RT + r], g[r][c], g[r][c + 1],
+                                 vv[i][e], vv[i][e + 1]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NVB; ++q) p[q] = s0[q] + s1[q];
+    }
+    cta_sum_n<T, G, NVB>(p, lane, warp, red, buf);
+    T tk[BB], al[BB][RT], be[BB][RT];
+#pragma unroll
+    for (int i = 0; i < BB; ++i) tk[i] = __ldg(tau + kk(i));
+#pragma unroll
+    for (int i = 0; i < BB; ++i) {
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            al[i][r] = p[i * RT + r];
+            be[i][r] = p[(BB + i) * RT + r];
+        }
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            // v_{k_i} . v_{k_j}: the band entry of the lower index at distance i - j
+            const T gij = __ldg(gram + (size_t)(DESC ? kk(i) : kk(j)) * 16 + (i - j));
+            const T tj = tk[j] * gij;
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                al[i][r] = fma(-tj, al[j][r], al[i][r]);
+                be[i][r] = fma(-tj, be[j][r], be[i][r]);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < BB; ++i) {
+            double ab = 0.0;
+#pragma unroll
+            for (int r = 0; r < RT; ++r) ab += (double)al[i][r] * (double)be[i][r];
+            sacc[kk(i)] += ab;
+        }
+    }
+#pragma unroll
+    for (int ig = 0; ig < NG; ++ig) {
+        T vv[BB][VEC], acc[BB][VEC];
+#pragma unroll
+        for (int i = 0; i < BB; ++i) {
+            fused::ldg_granule<T>(V + (size_t)kk(i) * ldv + (size_t)(t + G * ig) * VEC, vv[i]);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc[i][e] = T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; e += 2) {
+            const int c = ig * VEC + e;
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int i = 0; i < BB; ++i) {
+                    const T alpha = al[i][r], nb = -be[i][r];
+                    const T ca = -tk[i] * alpha, cb = -tk[i] * be[i][r];
+                    fma_pair(a[r][c], a[r][c + 1], ca, ca, vv[i][e], vv[i][e + 1]);           // a_in
+                    fma_pair(acc[i][e], acc[i][e + 1], nb, nb, a[r][c], a[r][c + 1]);        // - beta a_in
+                    fma_pair(acc[i][e], acc[i][e + 1], alpha, alpha, g[r][c], g[r][c + 1]);  // + alpha G
+                    fma_pair(g[r][c], g[r][c + 1], cb, cb, vv[i][e], vv[i][e + 1]);          // H G
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < BB; ++i) {
+            T *pk = accp + (size_t)kk(i) * COVER + (size_t)(t + G * ig) * VEC;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) pk[e] += acc[i][e];
+        }
+    }
+}
+
+// BB forward reflectors k0, k0 + 1, ... in one round: the BB dot products of
+// every row are taken at the round's start and reduced together, and
+// c_i = v_i . a - sum_{j<i} tau_j c_j (v_i . v_j) gives each reflector's value
+// (the forward chain's Gram correction).
+template <typename T, int G, int NG, int RT, int BB>
+__device__ __forceinline__ void forward_round(T (&a)[RT][BCfg<T, G, NG, RT>::E],
+                                              const T *__restrict__ V, int64_t ldv, int k0,
+                                              const T *__restrict__ tau,
+                                              const T *__restrict__ gram, int t, int lane,
+                                              int warp, T *red, int &buf) {
+    using C = BCfg<T, G, NG, RT>;
+    constexpr int VEC = C::VEC;
+    constexpr int NVB = BB * RT;
+    static_assert(VEC % 2 == 0, "columns go in pairs");
+    T p[NVB];
+    {
+        T s0[NVB], s1[NVB];
+#pragma unroll
+        for (int q = 0; q < NVB; ++q) s0[q] = s1[q] = T(0);
+#pragma unroll
+        for (int ig = 0; ig < NG; ++ig) {
+            T vv[BB][VEC];
+#pragma unroll
+            for (int i = 0; i < BB; ++i)
+                fused::ldg_granule<T>(V + (size_t)(k0 + i) * ldv + (size_t)(t + G * ig) * VEC, vv[i]);
+#pragma unroll
+            for (int e = 0; e < VEC; e += 2) {
+                const int c = ig * VEC + e;
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int i = 0; i < BB; ++i)
+                        fma_pair(s0[i * RT + r], s1[i * RT + r], a[r][c], a[r][c + 1], vv[i][e],
+                                 vv[i][e + 1]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NVB; ++q) p[q] = s0[q] + s1[q];
+    }
+    cta_sum_n<T, G, NVB>(p, lane, warp, red, buf);
+    T tk[BB], cf[BB][RT];
+#pragma unroll
+    for (int i = 0; i < BB; ++i) tk[i] = __ldg(tau + k0 + i);
+#pragma unroll
+    for (int i = 0; i < BB; ++i) {
+#pragma unroll
+        for (int r = 0; r < RT; ++r) cf[i][r] = p[i * RT + r];
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            const T tj = tk[j] * __ldg(gram + (size_t)(k0 + j) * 16 + (i - j));
+#pragma unroll
+            for (int r = 0; r < RT; ++r) cf[i][r] = fma(-tj, cf[j][r], cf[i][r]);
+        }
+    }
+#pragma unroll
+    for (int ig = 0; ig < NG; ++ig) {
+        T vv[BB][VEC];
+#pragma unroll
+        for (int i = 0; i < BB; ++i)
+            fused::ldg_granule<T>(V + (size_t)(k0 + i) * ldv + (size_t)(t + G * ig) * VEC, vv[i]);
+#pragma unroll
+        for (int e = 0; e < VEC; e += 2) {
+            const int c = ig * VEC + e;
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int i = 0; i < BB; ++i) {
+                    const T cc = -tk[i] * cf[i][r];
+                    fma_pair(a[r][c], a[r][c + 1], cc, cc, vv[i][e], vv[i][e + 1]);
+                }
+        }
+    }
+}
+
+// The forward chain k = 0 .. h-1 on the rows in a, in rounds of BB.
+template <typename T, int G, int NG, int RT, int BB>
+__device__ __forceinline__ void forward_walk(T (&a)[RT][BCfg<T, G, NG, RT>::E],
+                                             const T *__restrict__ V, int64_t ldv, int h,
+                                             const T *__restrict__ tau,
+                                             const T *__restrict__ gram, int t, int lane, int warp,
+                                             T *red, int &buf) {
+    using C = BCfg<T, G, NG, RT>;
+    int k = 0;
+    if constexpr (BB > 1)
+        for (; k + BB <= h; k += BB)
+            forward_round<T, G, NG, RT, BB>(a, V, ldv, k, tau, gram, t, lane, warp, red, buf);
+    for (; k < h; ++k) {
+        T v[C::E];
+        load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+        forward_step<T, G, NG, RT>(a, v, __ldg(tau + k), lane, warp, red, buf);
+    }
+}
+
+// The backward walk over all h reflectors: k = h-1 .. 0 (DESC) or 0 .. h-1,
+// in rounds of BB, the remainder one reflector per round.
+template <typename T, int G, int NG, int RT, int BB, bool DESC>
+__device__ __forceinline__ void backward_walk(T (&a)[RT][BCfg<T, G, NG, RT>::E],
+                                              T (&g)[RT][BCfg<T, G, NG, RT>::E],
+                                              const T *__restrict__ V, int64_t ldv, int h,
+                                              const T *__restrict__ tau,
+                                              const T *__restrict__ gram, T *accp, double *sacc,
+                                              int t, int lane, int warp, T *red, int &buf) {
+    using C = BCfg<T, G, NG, RT>;
+    constexpr int E = C::E, COVER = C::COVER;
+    int k = DESC ? h - 1 : 0, left = h;
+    if constexpr (BB > 1) {
+        for (; left >= BB; left -= BB, k += DESC ? -BB : BB)
+            backward_round<T, G, NG, RT, BB, DESC>(a, g, V, ldv, k, tau, gram, accp, sacc, t, lane,
+                                                   warp, red, buf);
+    }
+    for (; left > 0; --left, k += DESC ? -1 : 1) {
+        T v[E];
+        load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
+        backward_step<T, G, NG, RT>(a, g, v, __ldg(tau + k), accp + (size_t)k * COVER, sacc + k, t,
+                                    lane, warp, red, buf);
+    }
+}
+
 // Grid-persistent backward.  part: per CTA (h + 1) rows of COVER values
 // (rows k < h: P_k; row h: the dL/dd partial), spart: per CTA h doubles (s_k).
 // With SMEM the accumulators live in shared memory and are copied to `part`
@@ -251,18 +510,27 @@ __device__ __forceinline__ void load_pair_rows(T (&a)[RT][BCfg<T, G, NG, RT>::E]
     }
 }
 
-template <typename T, int MODE, int G, int NG, int RT, bool SMEM>
-__global__ void __launch_bounds__(G)
+// PRE (mode S): the forward states come precomputed in two row-major
+// batch x n arrays (leading dimension n): pre_a = W (d .* p) before the final
+// sign and pre_p = p.  The kernel then skips its own forward recompute and
+// holds no copy of p.  BB: reflectors per backward round (backward_round); FB:
+// per round of mode 3's forward recompute (forward_round).
+template <typename T, int MODE, int G, int NG, int RT, bool SMEM, bool PRE, int MINB, int BB,
+          int FB>
+__global__ void __launch_bounds__(G, MINB)
 backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_t ldgx,
                 int64_t batch, int n, const T *__restrict__ V, const T *__restrict__ tau,
                 int64_t ldv, int h, const T *__restrict__ sign, const T *__restrict__ d,
                 T *__restrict__ part, double *__restrict__ spart, int vec_ok,
                 const int64_t *__restrict__ ia, const int64_t *__restrict__ ib, int64_t nrows,
-                int *__restrict__ err) {
+                int *__restrict__ err, const T *__restrict__ pre_a, const T *__restrict__ pre_p,
+                int pre_vec_ok, const T *__restrict__ gram) {
     using C = BCfg<T, G, NG, RT>;
     constexpr int E = C::E, VEC = C::VEC, COVER = C::COVER;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[2 * C::NV * C::NW];
+    constexpr int NVMAX = C::NV > 2 * BB * RT ? (C::NV > FB * RT ? C::NV : FB * RT)
+                                              : (2 * BB * RT > FB * RT ? 2 * BB * RT : FB * RT);
+    __shared__ T red[2 * NVMAX * C::NW];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     T *accp = SMEM ? reinterpret_cast<T *>(smem_raw) : part + (size_t)blockIdx.x * (h + 1) * COVER;
     double *sacc = spart + (size_t)blockIdx.x * h;
@@ -279,20 +547,19 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int64_t r0 = tile * RT;
         T a[RT][E], g[RT][E], v[E];
-        T sg[E];
-        if (sign) load_cols<T, G, NG, RT>(sg, sign, t);
+        T sg[PRE ? 1 : E];
+        if constexpr (!PRE)
+            if (sign) load_cols<T, G, NG, RT>(sg, sign, t);
         if constexpr (MODE == kModeMahalanobis) {
             // z = W^T (sigma .* (x_a - x_b)); dL/dz = 2 g_p d .* z; dL/dd += g_p z .* z
+            static_assert(!PRE, "mode 3 recomputes z");
             load_pair_rows<T, G, NG, RT>(a, S, lds, nrows, ia, ib, r0, batch, n, t, vec_ok, err);
             if (sign)
 #pragma unroll
                 for (int r = 0; r < RT; ++r)
 #pragma unroll
                     for (int e = 0; e < E; ++e) a[r][e] *= sg[e];
-            for (int k = 0; k < h; ++k) {
-                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
-                forward_step<T, G, NG, RT>(a, v, __ldg(tau + k), lane, warp, red, buf);
-            }
+            forward_walk<T, G, NG, RT, FB>(a, V, ldv, h, tau, gram, t, lane, warp, red, buf);
             T dv[E], dd[E];
             load_cols<T, G, NG, RT>(dv, d, t);
 #pragma unroll
@@ -311,16 +578,15 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
             for (int i = 0; i < NG; ++i)
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) dk[(size_t)(t + G * i) * VEC + e] += dd[i * VEC + e];
-            for (int k = h - 1; k >= 0; --k) {
-                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
-                backward_step<T, G, NG, RT>(a, g, v, __ldg(tau + k), accp + (size_t)k * COVER,
-                                            sacc + k, t, lane, warp, red, buf);
-            }
+            backward_walk<T, G, NG, RT, BB, true>(a, g, V, ldv, h, tau, gram, accp, sacc, t, lane,
+                                                  warp, red, buf);
             continue;
         }
         load_rows<T, G, NG, RT>(g, gY, ldg, r0, batch, n, t, vec_ok);
-        T pvec[MODE == HH_MODE_SYM ? RT : 1][MODE == HH_MODE_SYM ? E : 1];
-        if (MODE == HH_MODE_SYM) {
+        T pvec[MODE == HH_MODE_SYM && !PRE ? RT : 1][MODE == HH_MODE_SYM && !PRE ? E : 1];
+        if (PRE && MODE == HH_MODE_SYM) {
+            load_rows<T, G, NG, RT>(a, pre_a, n, r0, batch, n, t, pre_vec_ok);
+        } else if (MODE == HH_MODE_SYM) {
             // recompute p = W^T (sigma .* x), then W (d .* p)
             load_rows<T, G, NG, RT>(a, S, lds, r0, batch, n, t, vec_ok);
             if (sign)
@@ -338,7 +604,7 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
             for (int r = 0; r < RT; ++r)
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    if constexpr (MODE == HH_MODE_SYM) pvec[r][e] = a[r][e];
+                    if constexpr (MODE == HH_MODE_SYM && !PRE) pvec[r][e] = a[r][e];
                     a[r][e] *= dv[e];
                 }
             for (int k = h - 1; k >= 0; --k) {
@@ -350,19 +616,26 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
         }
         // W part (modes W and S): y = sigma .* a^(1); walk k = 1..h
         if (MODE != HH_MODE_WT) {
-            if (sign)
+            if (sign) {
+                if constexpr (PRE) {
+                    T s1[E];
+                    load_cols<T, G, NG, RT>(s1, sign, t);
 #pragma unroll
-                for (int r = 0; r < RT; ++r)
+                    for (int r = 0; r < RT; ++r)
 #pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        if (MODE == HH_MODE_W) a[r][e] *= sg[e];
-                        g[r][e] *= sg[e];
-                    }
-            for (int k = 0; k < h; ++k) {
-                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
-                backward_step<T, G, NG, RT>(a, g, v, __ldg(tau + k), accp + (size_t)k * COVER,
-                                            sacc + k, t, lane, warp, red, buf);
+                        for (int e = 0; e < E; ++e) g[r][e] *= s1[e];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RT; ++r)
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            if (MODE == HH_MODE_W) a[r][e] *= sg[e];
+                            g[r][e] *= sg[e];
+                        }
+                }
             }
+            backward_walk<T, G, NG, RT, BB, false>(a, g, V, ldv, h, tau, gram, accp, sacc, t, lane,
+                                                   warp, red, buf);
         }
         if (MODE == HH_MODE_SYM) {
             // dL/dd += p .* dL/dq;  dL/dp = d .* dL/dq; continue from a = p
@@ -371,11 +644,14 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
             T dd[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) dd[e] = T(0);
+            if constexpr (PRE) load_rows<T, G, NG, RT>(a, pre_p, n, r0, batch, n, t, pre_vec_ok);
 #pragma unroll
             for (int r = 0; r < RT; ++r)
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    if constexpr (MODE == HH_MODE_SYM) {
+                    if constexpr (MODE == HH_MODE_SYM && PRE) {
+                        dd[e] = fma(a[r][e], g[r][e], dd[e]);
+                    } else if constexpr (MODE == HH_MODE_SYM) {
                         dd[e] = fma(pvec[r][e], g[r][e], dd[e]);
                         a[r][e] = pvec[r][e];
                     }
@@ -389,16 +665,23 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
         }
         // W^T part (modes WT and S): walk k = h..1; then dL/dx = sigma .* g
         if (MODE != HH_MODE_W) {
-            for (int k = h - 1; k >= 0; --k) {
-                load_cols<T, G, NG, RT>(v, V + (size_t)k * ldv, t);
-                backward_step<T, G, NG, RT>(a, g, v, __ldg(tau + k), accp + (size_t)k * COVER,
-                                            sacc + k, t, lane, warp, red, buf);
+            backward_walk<T, G, NG, RT, BB, true>(a, g, V, ldv, h, tau, gram, accp, sacc, t, lane,
+                                                  warp, red, buf);
+            if (sign) {
+                if constexpr (PRE) {
+                    T s1[E];
+                    load_cols<T, G, NG, RT>(s1, sign, t);
+#pragma unroll
+                    for (int r = 0; r < RT; ++r)
+#pragma unroll
+                        for (int e = 0; e < E; ++e) g[r][e] *= s1[e];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RT; ++r)
+#pragma unroll
+                        for (int e = 0; e < E; ++e) g[r][e] *= sg[e];
+                }
             }
-            if (sign)
-#pragma unroll
-                for (int r = 0; r < RT; ++r)
-#pragma unroll
-                    for (int e = 0; e < E; ++e) g[r][e] *= sg[e];
         }
         if (gX) {
 #pragma unroll
@@ -436,8 +719,12 @@ backward_kernel(const T *S, int64_t lds, const T *gY, int64_t ldg, T *gX, int64_
     }
 }
 
-// Fixed-order FP64 reduction of the partials.  Block k < h writes dL/dv_k
-// (gU row k, length n); block h writes dL/dd.
+// Fixed-order FP64 reduction of the partials.  Block (k, c) handles columns
+// 32c .. 32c+31 of row k: k < h writes dL/dv_k (gU row k, length n), k = h
+// writes dL/dd.  Each of 8 warps sums every 8th partial (warp w: parts
+// w, w + 8, ...), then one warp adds the 8 sums in order; s_k is summed
+// lane-strided with a fixed shuffle tree.  The result does not depend on the
+// launch, only on nparts.
 template <typename T>
 __global__ void __launch_bounds__(256)
 reduce_kernel(const T *__restrict__ part, const double *__restrict__ spart, int nparts, int cover,
@@ -446,19 +733,43 @@ reduce_kernel(const T *__restrict__ part, const double *__restrict__ spart, int 
     const int k = blockIdx.x;
     if (k < h && !gU) return;
     if (k == h && !gd) return;
-    double s = 0.0, t = 0.0;
-    if (k < h) {
-        for (int p = 0; p < nparts; ++p) s += spart[(size_t)p * h + k];
-        t = tau[k];
+    const int cx = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int j = blockIdx.y * 32 + cx;
+    __shared__ double sh[8][33];
+    __shared__ double ssum;
+    double acc = 0.0;
+    if (j < n)
+        for (int p = grp; p < nparts; p += 8) acc += (double)part[((size_t)p * (h + 1) + k) * cover + j];
+    sh[grp][cx] = acc;
+    if (k < h && grp == 0) {
+        double sk = 0.0;
+        for (int p = cx; p < nparts; p += 32) sk += spart[(size_t)p * h + k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sk += __shfl_xor_sync(0xffffffffu, sk, off);
+        if (cx == 0) ssum = sk;
     }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double acc = 0.0;
-        for (int p = 0; p < nparts; ++p) acc += (double)part[((size_t)p * (h + 1) + k) * cover + j];
-        if (k < h)
-            gU[(size_t)k * n + j] = (T)(t * acc - t * t * s * (double)V[(size_t)k * ldv + j]);
-        else
-            gd[j] = (T)acc;
+    __syncthreads();
+    if (grp == 0 && j < n) {
+        double tot = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tot += sh[q][cx];
+        if (k < h) {
+            const double t = tau[k];
+            gU[(size_t)k * n + j] = (T)(t * tot - t * t * ssum * (double)V[(size_t)k * ldv + j]);
+        } else {
+            gd[j] = (T)tot;
+        }
     }
+}
+
+// Q = d .* P (rows of length n, leading dimension n); one row per block step.
+template <typename T>
+__global__ void __launch_bounds__(256)
+scale_cols_kernel(const T *__restrict__ P, T *__restrict__ Q, const T *__restrict__ d,
+                  int64_t batch, int n) {
+    for (int64_t r = blockIdx.x; r < batch; r += gridDim.x)
+        for (int c = threadIdx.x; c < n; c += blockDim.x)
+            Q[r * n + c] = P[r * n + c] * __ldg(d + c);
 }
 
 struct PairArgs {
@@ -466,7 +777,7 @@ struct PairArgs {
     int64_t nrows = 0;
 };
 
-template <typename T, int G, int NG, int RT>
+template <typename T, int G, int NG, int RT, int MINB = 1, int BB = 1, int FB = 1>
 hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int64_t ldg,
               T *gX, int64_t ldgx, T *gU, T *gd, int64_t batch, int vec_ok, void *scratch,
               size_t scratch_bytes, PairArgs pa, cudaStream_t st) {
@@ -481,7 +792,18 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
         return nb;
     };
     const int64_t tiles = (batch + RT - 1) / RT;
-    auto launch = [&](auto kern, size_t smem) -> hh_status {
+    // Mode S in F32 on the allocating path: the forward states p and W (d .* p)
+    // come from the fused forward kernels (blocked rounds), and the adjoint
+    // kernel reads them instead of recomputing the chain one reflector per
+    // round.  Bounded to kPreMaxBytes of extra device memory; above it, or with
+    // a caller's scratch (no allocation allowed), the kernel recomputes.  (For
+    // mode 3 the gathered differences would cost more HBM traffic than the
+    // recompute saves.)
+    constexpr size_t kPreMaxBytes = size_t(2) << 30;
+    const size_t pre_bytes = (size_t)batch * n * sizeof(T) * 2;
+    const bool pre = std::is_same<T, float>::value && !scratch && batch > 0 && n % 4 == 0 &&
+                     mode == HH_MODE_SYM && pre_bytes <= kPreMaxBytes;
+    auto launch = [&](auto kern, size_t smem, bool with_pre) -> hh_status {
         int nparts = (int)std::min<int64_t>(tiles, (int64_t)p->num_sms * pick(kern, smem));
         if (nparts < 1) nparts = 1;
         const size_t need = (size_t)nparts * (acc_bytes + (size_t)h * sizeof(double));
@@ -504,35 +826,73 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
         T *part = reinterpret_cast<T *>(buf);
         double *spart = reinterpret_cast<double *>(reinterpret_cast<char *>(buf) +
                                                    (size_t)nparts * acc_bytes);
-        kern<<<nparts, G, smem, st>>>(S, lds, gY, ldg, gX, ldgx, batch, n, (const T *)p->u,
-                                      (const T *)p->tau_t, p->ldv, h, (const T *)p->sign,
-                                      (const T *)p->d, part, spart, vec_ok, pa.ia, pa.ib,
-                                      pa.nrows, p->err);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess && (gU || gd))
-            reduce_kernel<T><<<h + 1, 256, 0, st>>>(part, spart, nparts, C::COVER, n, h,
-                                                    (const T *)p->u, p->ldv, p->tau, gU, gd);
+        T *pre_buf = nullptr, *pre_a = nullptr, *pre_p = nullptr;
+        cudaError_t e = cudaSuccess;
+        hh_status hs = HH_OK;
+        if (with_pre) {
+            e = dev_malloc_async(reinterpret_cast<void **>(&pre_buf), pre_bytes, st);
+            if (e != cudaSuccess) {
+                if (own) cudaFreeAsync(buf, st);
+                return cuda_fail(e, "cudaMallocAsync (backward forward states)");
+            }
+            const unsigned fill = (unsigned)std::min<int64_t>(batch, (int64_t)p->num_sms * 8);
+            // p = W^T (sigma .* x); q = W (d .* p) without the final sign
+            pre_p = pre_buf;
+            pre_a = pre_buf + (size_t)batch * n;
+            hs = fused_apply(p, HH_MODE_WT, S, lds, pre_p, n, batch, st);
+            if (hs == HH_OK) {
+                scale_cols_kernel<T><<<fill, 256, 0, st>>>(pre_p, pre_a, (const T *)p->d, batch, n);
+                e = cudaGetLastError();
+            }
+            if (hs == HH_OK && e == cudaSuccess) {
+                Plan unsigned_plan = *p;
+                unsigned_plan.sign = nullptr;
+                hs = fused_apply(&unsigned_plan, HH_MODE_W, pre_a, n, pre_a, n, batch, st);
+            }
+        }
+        if (hs == HH_OK && e == cudaSuccess) {
+            kern<<<nparts, G, smem, st>>>(S, lds, gY, ldg, gX, ldgx, batch, n, (const T *)p->u,
+                                          (const T *)p->tau_t, p->ldv, h, (const T *)p->sign,
+                                          (const T *)p->d, part, spart, vec_ok, pa.ia, pa.ib,
+                                          pa.nrows, p->err, pre_a, pre_p, 1,
+                                          (const T *)p->gram);
+            e = cudaGetLastError();
+        }
+        if (hs == HH_OK && e == cudaSuccess && (gU || gd))
+            reduce_kernel<T><<<dim3(h + 1, (n + 31) / 32), 256, 0, st>>>(
+                part, spart, nparts, C::COVER, n, h, (const T *)p->u, p->ldv, p->tau, gU, gd);
         if (e == cudaSuccess) e = cudaGetLastError();
+        if (pre_buf) {
+            cudaError_t e2 = cudaFreeAsync(pre_buf, st);
+            if (e == cudaSuccess) e = e2;
+        }
         if (own) {
             cudaError_t e2 = cudaFreeAsync(buf, st);
             if (e == cudaSuccess) e = e2;
         }
+        if (hs != HH_OK) return hs;
         if (e != cudaSuccess) return cuda_fail(e, "backward launch");
         return HH_OK;
     };
-#define HH_BWD_MODE(M)                                                  \
-    if (use_smem) {                                                     \
-        return launch(backward_kernel<T, M, G, NG, RT, true>, acc_bytes); \
-    } else {                                                            \
-        return launch(backward_kernel<T, M, G, NG, RT, false>, 0);      \
+// Mode S without PRE holds p as well: one reflector per round there (the
+// blocked round's extra registers would spill).
+#define HH_BWD_KERN(M, PRE, BBX)                                                              \
+    if (use_smem) {                                                                           \
+        return launch(backward_kernel<T, M, G, NG, RT, true, PRE, MINB, BBX, FB>, acc_bytes, PRE); \
+    } else {                                                                                  \
+        return launch(backward_kernel<T, M, G, NG, RT, false, PRE, MINB, BBX, FB>, 0, PRE);       \
     }
     switch (mode) {
-        case HH_MODE_W: HH_BWD_MODE(HH_MODE_W)
-        case HH_MODE_WT: HH_BWD_MODE(HH_MODE_WT)
-        case HH_MODE_SYM: HH_BWD_MODE(HH_MODE_SYM)
-        default: HH_BWD_MODE(kModeMahalanobis)
+        case HH_MODE_W: HH_BWD_KERN(HH_MODE_W, false, BB)
+        case HH_MODE_WT: HH_BWD_KERN(HH_MODE_WT, false, BB)
+        case HH_MODE_SYM:
+            if constexpr (std::is_same<T, float>::value) {
+                if (pre) HH_BWD_KERN(HH_MODE_SYM, true, BB)
+            }
+            HH_BWD_KERN(HH_MODE_SYM, false, 1)
+        default: HH_BWD_KERN(kModeMahalanobis, false, BB)
     }
-#undef HH_BWD_MODE
+#undef HH_BWD_KERN
 }
 
 template <typename T>
@@ -546,15 +906,34 @@ hh_status dispatch(const Plan *p, int mode, const void *S, int64_t lds, const vo
                        (mode == kModeMahalanobis ||
                         ((uintptr_t)gY % 16 == 0 && ldg % vec == 0 &&
                          (!gX || ((uintptr_t)gX % 16 == 0 && ldgx % vec == 0))));
-#define HH_RUN(G, NG, RT)                                                                   \
-    return run<T, G, NG, RT>(p, mode, (const T *)S, lds, (const T *)gY, ldg, (T *)gX, ldgx, \
+#define HH_RUN(G, NG, RT) HH_RUN_B(G, NG, RT, 1, 1, 1)
+#define HH_RUN_B(G, NG, RT, MINB, BB, FB)                                                   \
+    return run<T, G, NG, RT, MINB, BB, FB>(p, mode, (const T *)S, lds, (const T *)gY, ldg, (T *)gX, ldgx, \
                              (T *)gU, (T *)gd, batch, vec_ok, scratch, scratch_bytes, pa, st)
-    if (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4) {
         if (n <= 128) HH_RUN(32, 1, 4);
 #ifndef HH_BWD256_G
 #define HH_BWD256_G 32
 #define HH_BWD256_NG 2
 #define HH_BWD256_RT HH_BWD_RT
+#endif
+#ifndef HH_BWD256_MINB
+#define HH_BWD256_MINB 1
+#endif
+#ifndef HH_BWD1024_MINB
+#define HH_BWD1024_MINB 1
+#endif
+#ifndef HH_BWD256_BB
+#define HH_BWD256_BB 2
+#endif
+#ifndef HH_BWD256_FB
+#define HH_BWD256_FB 4
+#endif
+#ifndef HH_BWD1024_BB
+#define HH_BWD1024_BB 2
+#endif
+#ifndef HH_BWD1024_FB
+#define HH_BWD1024_FB 1
 #endif
 #ifndef HH_BWD1024_G
 // 4 rows x 16 columns per thread, two warps per row (measured 14% faster than
@@ -563,9 +942,11 @@ hh_status dispatch(const Plan *p, int mode, const void *S, int64_t lds, const vo
 #define HH_BWD1024_NG 4
 #define HH_BWD1024_RT 4
 #endif
-        if (n <= 256) HH_RUN(HH_BWD256_G, HH_BWD256_NG, HH_BWD256_RT);
+        if (n <= 256) HH_RUN_B(HH_BWD256_G, HH_BWD256_NG, HH_BWD256_RT, HH_BWD256_MINB, HH_BWD256_BB,
+                                HH_BWD256_FB);
         if (n <= 512) HH_RUN(64, 2, HH_BWD_RT);
-        if (n <= 1024) HH_RUN(HH_BWD1024_G, HH_BWD1024_NG, HH_BWD1024_RT);
+        if (n <= 1024) HH_RUN_B(HH_BWD1024_G, HH_BWD1024_NG, HH_BWD1024_RT, HH_BWD1024_MINB,
+                                 HH_BWD1024_BB, HH_BWD1024_FB);
         if (n <= 2048) HH_RUN(256, 2, 2);
         if (n <= 4096) HH_RUN(512, 2, 2);
     } else {
@@ -577,6 +958,7 @@ hh_status dispatch(const Plan *p, int mode, const void *S, int64_t lds, const vo
         if (n <= 2048) HH_RUN(512, 2, 2);
     }
 #undef HH_RUN
+#undef HH_RUN_B
     return fail(HH_ERR_UNSUPPORTED, "backward: n = %lld is above this build's limit (%d)",
                 (long long)n, sizeof(T) == 4 ? 4096 : 2048);
 }

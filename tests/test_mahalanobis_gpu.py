@@ -86,6 +86,29 @@ def test_mahalanobis_bad_index_reported():
     plan.sync()  # the status word was cleared
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_mahalanobis_gradient_bad_index_reported(dtype):
+    """An out-of-range index in the gradient call is reported, and its pair
+    contributes nothing: the gradients equal those of the valid pairs alone."""
+    from paper_1811_07624_gb300 import HHError
+
+    plan, Xg, iag, ibg, U, d, s, X, ia, ib = _setup(64, 5, 40, 30, dtype, seed=9)
+    g = torch.ones(ia.shape[0], dtype=dtype, device=DEV)
+    bad_a, bad_b = iag.clone(), ibg.clone()
+    bad_a[3], bad_b[7] = 40, -1
+    gU, gd = plan.mahalanobis_backward(Xg, bad_a, bad_b, g)
+    with pytest.raises(HHError) as ei:
+        plan.sync()
+    assert ei.value.code == "HH_ERR_INVALID_ARG"
+    keep = torch.ones(ia.shape[0], dtype=torch.bool, device=DEV)
+    keep[3] = keep[7] = False
+    gU_ref, gd_ref = plan.mahalanobis_backward(Xg, iag[keep], ibg[keep], g[keep])
+    plan.sync()
+    tol = 1e-5 if dtype == torch.float32 else 1e-12
+    assert _rel(gU.double().cpu().numpy(), gU_ref.double().cpu().numpy()) <= tol
+    assert _rel(gd.double().cpu().numpy(), gd_ref.double().cpu().numpy()) <= tol
+
+
 def test_mahalanobis_gradcheck_f64():
     from paper_1811_07624_gb300 import autograd
 
