@@ -762,14 +762,20 @@ reduce_kernel(const T *__restrict__ part, const double *__restrict__ spart, int 
     }
 }
 
-// Q = d .* P (rows of length n, leading dimension n); one row per block step.
-template <typename T>
+// Q = d .* P (rows of length n, leading dimension n, n % 4 == 0, both 16-byte
+// aligned): one 4-column granule per thread, grid-stride.
 __global__ void __launch_bounds__(256)
-scale_cols_kernel(const T *__restrict__ P, T *__restrict__ Q, const T *__restrict__ d,
+scale_cols_kernel(const float *__restrict__ P, float *__restrict__ Q, const float *__restrict__ d,
                   int64_t batch, int n) {
-    for (int64_t r = blockIdx.x; r < batch; r += gridDim.x)
-        for (int c = threadIdx.x; c < n; c += blockDim.x)
-            Q[r * n + c] = P[r * n + c] * __ldg(d + c);
+    const int ng = n / 4;
+    const int64_t total = batch * ng;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ng) * 4;
+        const float4 x = reinterpret_cast<const float4 *>(P)[i];
+        const float4 s = *reinterpret_cast<const float4 *>(d + c);
+        reinterpret_cast<float4 *>(Q)[i] = make_float4(x.x * s.x, x.y * s.y, x.z * s.z, x.w * s.w);
+    }
 }
 
 struct PairArgs {
@@ -835,13 +841,15 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
                 if (own) cudaFreeAsync(buf, st);
                 return cuda_fail(e, "cudaMallocAsync (backward forward states)");
             }
-            const unsigned fill = (unsigned)std::min<int64_t>(batch, (int64_t)p->num_sms * 8);
+            const unsigned fill =
+                (unsigned)std::min<int64_t>((batch * (n / 4) + 255) / 256, (int64_t)p->num_sms * 8);
             // p = W^T (sigma .* x); q = W (d .* p) without the final sign
             pre_p = pre_buf;
             pre_a = pre_buf + (size_t)batch * n;
             hs = fused_apply(p, HH_MODE_WT, S, lds, pre_p, n, batch, st);
             if (hs == HH_OK) {
-                scale_cols_kernel<T><<<fill, 256, 0, st>>>(pre_p, pre_a, (const T *)p->d, batch, n);
+                scale_cols_kernel<<<fill, 256, 0, st>>>((const float *)pre_p, (float *)pre_a,
+                                                        (const float *)p->d, batch, n);
                 e = cudaGetLastError();
             }
             if (hs == HH_OK && e == cudaSuccess) {
