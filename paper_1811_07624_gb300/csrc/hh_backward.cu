@@ -29,6 +29,12 @@
 
 #include "hh_fused.cuh"
 
+// Mode S in F32 (allocating path): P_k through batch contractions (1) or
+// accumulated per tile by the adjoint kernel (0).
+#ifndef HH_BWD_SYM_CONTRACT
+#define HH_BWD_SYM_CONTRACT 1
+#endif
+
 // Rows per thread of the F32 adjoint for 128 < n <= 512 (and the default of the
 // compile-time shape overrides below).
 #ifndef HH_BWD_RT
@@ -778,6 +784,527 @@ scale_cols_kernel(const float *__restrict__ P, float *__restrict__ Q, const floa
     }
 }
 
+// ---- mode S in F32 through batch contractions ------------------------------------------
+//
+// With (A, G) the state a walk starts from and a^(k), g^(k) the state when it
+// reaches reflector k, both are the start state minus multiples of the
+// reflectors walked before: a^(k) = A - sum_{j before k} tau_j alpha_j v_j,
+// and g^(k) likewise with beta.  So the per-reflector partial of the walk,
+//     P_k = sum_rows alpha_k g^(k) - beta_k a^(k+)      (a^(k+): after H_k),
+// splits into two products over the batch and a combination of reflectors:
+//     P_k = G^T alpha_k - A^T beta_k - sum_{j before k} tau_j M[k][j] v_j
+//           + sum_{j up to k} tau_j M[j][k] v_j,        M = alpha^T beta (h x h).
+// The walk kernel writes each row's alpha_k and -beta_k and the state G of the
+// second walk; G^T alpha - A^T beta and M are batch contractions (xty_kernel,
+// FP32 within a chunk of rows, FP64 across chunks in a fixed order), and
+// combine_kernel forms
+// dL/dv_k = tau_k P_k - tau_k^2 s_k v_k with s_k = M[k][k].  The same
+// quantities as the per-tile accumulation, summed in a different order.
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One walk round without accumulation: as backward_round, then the rows'
+// alpha and -beta of the round's reflectors go to Aout, Bout (batch x h).
+template <int G, int NG, int RT, int BB, bool DESC>
+__device__ __forceinline__ void walk_round(float (&a)[RT][BCfg<float, G, NG, RT>::E],
+                                           float (&g)[RT][BCfg<float, G, NG, RT>::E],
+                                           const float *__restrict__ V, int64_t ldv, int k0,
+                                           const float *__restrict__ tau,
+                                           const float *__restrict__ gram, float *Aout,
+                                           float *Bout, int64_t r0, int64_t batch, int h, int t,
+                                           int lane, int warp, float *red, int &buf) {
+    using C = BCfg<float, G, NG, RT>;
+    constexpr int VEC = C::VEC;
+    constexpr int NVB = 2 * BB * RT;
+    auto kk = [&](int i) { return DESC ? k0 - i : k0 + i; };
+    float p[NVB];
+    {
+        float s0[NVB], s1[NVB];
+#pragma unroll
+        for (int q = 0; q < NVB; ++q) s0[q] = s1[q] = 0.f;
+#pragma unroll
+        for (int ig = 0; ig < NG; ++ig) {
+            float vv[BB][VEC];
+#pragma unroll
+            for (int i = 0; i < BB; ++i)
+                fused::ldg_granule<float>(V + (size_t)kk(i) * ldv + (size_t)(t + G * ig) * VEC, vv[i]);
+#pragma unroll
+            for (int e = 0; e < VEC; e += 2) {
+                const int c = ig * VEC + e;
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+#pragma unroll
+                    for (int i = 0; i < BB; ++i) {
+                        fma_pair(s0[i * RT + r], s1[i * RT + r], a[r][c], a[r][c + 1], vv[i][e],
+                                 vv[i][e + 1]);
+                        fma_pair(s0[(BB + i) * RT + r], s1[(BB + i) * RT + r], g[r][c], g[r][c + 1],
+                                 vv[i][e], vv[i][e + 1]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NVB; ++q) p[q] = s0[q] + s1[q];
+    }
+    cta_sum_n<float, G, NVB>(p, lane, warp, red, buf);
+    float tk[BB], al[BB][RT], be[BB][RT];
+#pragma unroll
+    for (int i = 0; i < BB; ++i) tk[i] = __ldg(tau + kk(i));
+#pragma unroll
+    for (int i = 0; i < BB; ++i) {
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            al[i][r] = p[i * RT + r];
+            be[i][r] = p[(BB + i) * RT + r];
+        }
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            const float gij = __ldg(gram + (size_t)(DESC ? kk(i) : kk(j)) * 16 + (i - j));
+            const float tj = tk[j] * gij;
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                al[i][r] = fmaf(-tj, al[j][r], al[i][r]);
+                be[i][r] = fmaf(-tj, be[j][r], be[i][r]);
+            }
+        }
+    }
+    // thread r writes row r's values (every thread holds all of them)
+#pragma unroll
+    for (int r = 0; r < RT; ++r)
+        if (t == r && r0 + r < batch)
+#pragma unroll
+            for (int i = 0; i < BB; ++i) {
+                Aout[(size_t)(r0 + r) * h + kk(i)] = al[i][r];
+                Bout[(size_t)(r0 + r) * h + kk(i)] = -be[i][r];
+            }
+#pragma unroll
+    for (int ig = 0; ig < NG; ++ig) {
+        float vv[BB][VEC];
+#pragma unroll
+        for (int i = 0; i < BB; ++i)
+            fused::ldg_granule<float>(V + (size_t)kk(i) * ldv + (size_t)(t + G * ig) * VEC, vv[i]);
+#pragma unroll
+        for (int e = 0; e < VEC; e += 2) {
+            const int c = ig * VEC + e;
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int i = 0; i < BB; ++i) {
+                    const float ca = -tk[i] * al[i][r], cb = -tk[i] * be[i][r];
+                    fma_pair(a[r][c], a[r][c + 1], ca, ca, vv[i][e], vv[i][e + 1]);
+                    fma_pair(g[r][c], g[r][c + 1], cb, cb, vv[i][e], vv[i][e + 1]);
+                }
+        }
+    }
+}
+
+// A whole walk (k = 0 .. h-1, or h-1 .. 0 with DESC) in rounds of BB.
+template <int G, int NG, int RT, int BB, bool DESC>
+__device__ __forceinline__ void walk_all(float (&a)[RT][BCfg<float, G, NG, RT>::E],
+                                         float (&g)[RT][BCfg<float, G, NG, RT>::E],
+                                         const float *__restrict__ V, int64_t ldv, int h,
+                                         const float *__restrict__ tau,
+                                         const float *__restrict__ gram, float *Aout, float *Bout,
+                                         int64_t r0, int64_t batch, int t, int lane, int warp,
+                                         float *red, int &buf) {
+    int k = DESC ? h - 1 : 0, left = h;
+    for (; left >= BB; left -= BB, k += DESC ? -BB : BB)
+        walk_round<G, NG, RT, BB, DESC>(a, g, V, ldv, k, tau, gram, Aout, Bout, r0, batch, h, t,
+                                        lane, warp, red, buf);
+    for (; left > 0; --left, k += DESC ? -1 : 1)
+        walk_round<G, NG, RT, 1, DESC>(a, g, V, ldv, k, tau, gram, Aout, Bout, r0, batch, h, t,
+                                       lane, warp, red, buf);
+}
+
+// The two walks of the mode-S adjoint from the precomputed states Q = W (d .* p)
+// (before the final sign) and P = p: the W walk from (Q, sigma .* dL/dy), then
+// dL/dd += p .* g, g = d .* g (written to Gd: the second walk's start), the
+// W^T walk from (P, Gd), and dL/dx = sigma .* g.  Per CTA the dL/dd partial
+// (COVER values) goes to ddpart.
+template <int G, int NG, int RT, int BB>
+__global__ void __launch_bounds__(G)
+sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t batch, int n,
+                const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv, int h,
+                const float *__restrict__ sign, const float *__restrict__ d,
+                const float *__restrict__ gram, const float *__restrict__ Q,
+                const float *__restrict__ P, float *__restrict__ Gd, float *__restrict__ AW,
+                float *__restrict__ BW, float *__restrict__ AT, float *__restrict__ BT,
+                float *__restrict__ ddpart, int vec_ok) {
+    using C = BCfg<float, G, NG, RT>;
+    constexpr int E = C::E, VEC = C::VEC, COVER = C::COVER;
+    constexpr int NVMAX = 2 * BB * RT > C::NV ? 2 * BB * RT : C::NV;
+    __shared__ float red[2 * NVMAX * C::NW];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    float dd[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) dd[e] = 0.f;
+    int buf = 0;
+    const int64_t tiles = (batch + RT - 1) / RT;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t r0 = tile * RT;
+        float a[RT][E], g[RT][E];
+        load_rows<float, G, NG, RT>(g, gY, ldg, r0, batch, n, t, vec_ok);
+        load_rows<float, G, NG, RT>(a, Q, n, r0, batch, n, t, 1);
+        if (sign) {
+            float s1[E];
+            load_cols<float, G, NG, RT>(s1, sign, t);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int e = 0; e < E; ++e) g[r][e] *= s1[e];
+        }
+        walk_all<G, NG, RT, BB, false>(a, g, V, ldv, h, tau, gram, AW, BW, r0, batch, t, lane, warp,
+                                       red, buf);
+        load_rows<float, G, NG, RT>(a, P, n, r0, batch, n, t, 1);
+        {
+            float dv[E];
+            load_cols<float, G, NG, RT>(dv, d, t);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    dd[e] = fmaf(a[r][e], g[r][e], dd[e]);
+                    g[r][e] *= dv[e];
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const int64_t row = r0 + r;
+            if (row >= batch) continue;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const int col = (t + G * i) * VEC;
+                float q[VEC];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) q[e] = g[r][i * VEC + e];
+                if (col + VEC <= n) fused::store_granule<float>(Gd + row * n + col, q);
+            }
+        }
+        walk_all<G, NG, RT, BB, true>(a, g, V, ldv, h, tau, gram, AT, BT, r0, batch, t, lane, warp,
+                                      red, buf);
+        if (gX) {
+            float s1[E];
+            if (sign) load_cols<float, G, NG, RT>(s1, sign, t);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const int64_t row = r0 + r;
+                if (row >= batch) continue;
+                float *gr = gX + row * ldgx;
+#pragma unroll
+                for (int i = 0; i < NG; ++i) {
+                    const int col = (t + G * i) * VEC;
+                    float q[VEC];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e)
+                        q[e] = sign ? g[r][i * VEC + e] * s1[i * VEC + e] : g[r][i * VEC + e];
+                    if (vec_ok && col + VEC <= n) {
+                        fused::store_granule<float>(gr + col, q);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e)
+                            if (col + e < n) gr[col + e] = q[e];
+                    }
+                }
+            }
+        }
+    }
+    float *dst = ddpart + (size_t)blockIdx.x * COVER;
+#pragma unroll
+    for (int i = 0; i < NG; ++i)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) dst[(size_t)(t + G * i) * VEC + e] = dd[i * VEC + e];
+}
+
+// Batch contraction out[c][k][j] = sum_pairs sum_{rows in chunk c} X[row][j] Y[row][k]
+// (j < n, k < h), the sum of pair 0 scaled by post0[j] when given.  X row-major
+// with 16-byte aligned rows (n % 4 == 0), Y row-major batch x h (h % 4 == 0).
+// A CTA of 64 threads computes a 128 x 32 (j x k) tile of one chunk, 8 x 8 per
+// thread in FP32 registers, over slabs of 16 rows moved into shared memory by
+// cp.async in a three-stage ring.  Chunk c covers rows [c*chunk, (c+1)*chunk).
+struct XtyArgs {
+    const float *X[4];
+    int64_t ldx[4];
+    const float *Y[4];
+    int npairs;
+    const float *post0;
+    int64_t rows, chunk;
+    int n, h;
+    float *out;  // nchunks x h x n
+};
+constexpr int kXtyJ = 128, kXtyK = 32, kXtySlab = 16, kXtyStages = 3;
+
+__global__ void __launch_bounds__(64)
+xty_kernel(const __grid_constant__ XtyArgs args) {
+    __shared__ __align__(16) float xs[kXtyStages][kXtySlab][kXtyJ];
+    __shared__ __align__(16) float ys[kXtyStages][kXtySlab][kXtyK];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int j0 = blockIdx.x * kXtyJ, k0 = blockIdx.y * kXtyK;
+    const int64_t rb = (int64_t)blockIdx.z * args.chunk;
+    const int64_t re = min(args.rows, rb + args.chunk);
+    const int n = args.n, h = args.h;
+    const int64_t nsl = re > rb ? (re - rb + kXtySlab - 1) / kXtySlab : 0;
+    const int64_t total = nsl * args.npairs;
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int w = 0; w < 8; ++w) acc[u][w] = 0.f;
+    auto issue = [&](int64_t s) {
+        const int stg = (int)(s % kXtyStages);
+        const int pi = (int)(s / nsl);
+        const int64_t r = rb + (s - pi * nsl) * kXtySlab;
+        const float *X = args.X[pi], *Y = args.Y[pi];
+        const int64_t ldx = args.ldx[pi];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int gi = t + 64 * q, rr = gi >> 5, cg = (gi & 31) * 4;
+            const int64_t row = r + rr;
+            const int col = j0 + cg;
+            const bool ok = row < re && col < n;
+            cp_async16(&xs[stg][rr][cg], ok ? X + row * ldx + col : X, ok ? 16 : 0);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int gi = t + 64 * q, rr = gi >> 3, kc = (gi & 7) * 4;
+            const int64_t row = r + rr;
+            const int k = k0 + kc;
+            const bool ok = row < re && k < h;
+            cp_async16(&ys[stg][rr][kc], ok ? Y + row * h + k : Y, ok ? 16 : 0);
+        }
+    };
+    auto post_scale = [&]() {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = j0 + (u < 4 ? tx * 4 + u : 64 + tx * 4 + (u - 4));
+            const float sc = j < n ? args.post0[j] : 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) acc[u][w] *= sc;
+        }
+    };
+#pragma unroll
+    for (int s = 0; s < kXtyStages - 1; ++s) {
+        if (s < total) issue(s);
+        cp_async_commit();
+    }
+    for (int64_t s = 0; s < total; ++s) {
+        if (s + kXtyStages - 1 < total) issue(s + kXtyStages - 1);
+        cp_async_commit();
+        cp_async_wait<kXtyStages - 1>();
+        __syncthreads();
+        if (s == nsl && args.post0) post_scale();
+        const int stg = (int)(s % kXtyStages);
+#pragma unroll
+        for (int q = 0; q < kXtySlab; ++q) {
+            const float4 xa = *reinterpret_cast<const float4 *>(&xs[stg][q][tx * 4]);
+            const float4 xb = *reinterpret_cast<const float4 *>(&xs[stg][q][64 + tx * 4]);
+            const float4 ya = *reinterpret_cast<const float4 *>(&ys[stg][q][ty * 4]);
+            const float4 yb = *reinterpret_cast<const float4 *>(&ys[stg][q][16 + ty * 4]);
+            const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+            const float yv[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int w = 0; w < 8; w += 2)
+                    fma_pair(acc[u][w], acc[u][w + 1], xv[u], xv[u], yv[w], yv[w + 1]);
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    if (args.npairs == 1 && args.post0) post_scale();
+    float *o = args.out + (size_t)blockIdx.z * h * n;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int j = j0 + (u < 4 ? tx * 4 + u : 64 + tx * 4 + (u - 4));
+        if (j >= n) continue;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int k = k0 + (w < 4 ? ty * 4 + w : 16 + ty * 4 + (w - 4));
+            if (k < h) o[(size_t)k * n + j] = acc[u][w];
+        }
+    }
+}
+
+// out[i] = sum over p of in[p * stride + i] in FP64 (i < count), p increasing
+// within each of 8 interleaved groups, the groups added in order.  Block b
+// handles i in [32b, 32b + 32).
+__global__ void __launch_bounds__(256)
+sum_parts_kernel(const float *__restrict__ in, int nparts, int64_t stride, int64_t count,
+                 double *__restrict__ out) {
+    __shared__ double sh[8][33];
+    const int cx = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + cx;
+    double s = 0.0;
+    if (i < count)
+        for (int p = grp; p < nparts; p += 8) s += (double)in[(size_t)p * stride + i];
+    sh[grp][cx] = s;
+    __syncthreads();
+    if (grp == 0 && i < count) {
+        double tot = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tot += sh[q][cx];
+        out[i] = tot;
+    }
+}
+
+// dL/dv_k (row k of gU) = tau_k P_k - tau_k^2 s_k v_k with
+// P_k = Pst[k] + sum_i Cf[k][i] v_i, where for each walk (MW: k = 0 .. h-1
+// first to last; MT: k = h-1 .. 0; the arrays hold -M, M[k][i] = sum_rows
+// alpha_k beta_i)
+//     Cf[k][i] += -tau_i M[k][i] [i walked before k] + tau_i M[i][k] [i walked up to k]
+// and s_k = MW[k][k] + MT[k][k].  Block (h, *) writes dL/dd.  Grid (h + 1,
+// column blocks of 256).
+__global__ void __launch_bounds__(256)
+combine_kernel(const double *__restrict__ Pst, const double *__restrict__ MW,
+               const double *__restrict__ MT, const double *__restrict__ tau,
+               const float *__restrict__ V, int64_t ldv, int n, int h, float *gU,
+               const double *__restrict__ dd, float *gd) {
+    const int k = blockIdx.x;
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k == h) {
+        if (gd && j < n) gd[j] = (float)dd[j];
+        return;
+    }
+    if (!gU) return;
+    extern __shared__ double cf[];  // h coefficients
+    for (int i = threadIdx.x; i < h; i += blockDim.x) {
+        double c = 0.0;
+        if (i < k) c += tau[i] * MW[(size_t)k * h + i];
+        if (i <= k) c -= tau[i] * MW[(size_t)i * h + k];
+        if (i > k) c += tau[i] * MT[(size_t)k * h + i];
+        if (i >= k) c -= tau[i] * MT[(size_t)i * h + k];
+        cf[i] = c;
+    }
+    __syncthreads();
+    if (j >= n) return;
+    const double tk = tau[k];
+    const double sk = -(MW[(size_t)k * h + k] + MT[(size_t)k * h + k]);
+    double pk = Pst[(size_t)k * n + j];
+    for (int i = 0; i < h; ++i) pk += cf[i] * (double)V[(size_t)i * ldv + j];
+    gU[(size_t)k * n + j] = (float)(tk * pk - tk * tk * sk * (double)V[(size_t)k * ldv + j]);
+}
+
+// Mode S, F32, allocating path, aligned dL/dy rows, h % 4 == 0, h <= 64:
+// forward states by the fused kernels, the walks by sym_walk_kernel, P_k by
+// the batch contraction, combine_kernel.
+template <int G, int NG, int RT, int BB>
+hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *gY, int64_t ldg,
+                       float *gX, int64_t ldgx, float *gU, float *gd, int64_t batch, int vec_ok,
+                       cudaStream_t st) {
+    using C = BCfg<float, G, NG, RT>;
+    const int h = (int)p->h, n = (int)p->n;
+    const size_t bn = (size_t)batch * n, bh = (size_t)batch * h;
+    auto kern = sym_walk_kernel<G, NG, RT, BB>;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, G, 0) != cudaSuccess || nb < 1) nb = 1;
+    const int64_t tiles = (batch + RT - 1) / RT;
+    const int nparts = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)p->num_sms * nb));
+    const int jt = (n + kXtyJ - 1) / kXtyJ, kt = (h + kXtyK - 1) / kXtyK;
+    const int64_t want = std::max<int64_t>(1, (int64_t)p->num_sms * 8 / (jt * kt));
+    int64_t chunk = std::max<int64_t>(256, (batch + want - 1) / want);
+    chunk = (chunk + kXtySlab - 1) / kXtySlab * kXtySlab;
+    const int nchunks = (int)((batch + chunk - 1) / chunk);
+    // one allocation, carved in 256-byte aligned pieces
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t oP = take(bn * 4), oQ = take(bn * 4), oGd = take(bn * 4);
+    const size_t oAW = take(bh * 4), oBW = take(bh * 4), oAT = take(bh * 4), oBT = take(bh * 4);
+    const size_t odd = take((size_t)nparts * C::COVER * 4);
+    const size_t oPp = take((size_t)nchunks * h * n * 4);
+    const size_t oMp = take((size_t)nchunks * 2 * h * h * 4);
+    const size_t oPst = take((size_t)h * n * 8), oM = take((size_t)2 * h * h * 8),
+                 odd64 = take((size_t)n * 8);
+    char *base = nullptr;
+    cudaError_t e = dev_malloc_async(reinterpret_cast<void **>(&base), off, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (adjoint work arrays)");
+    auto F = [&](size_t o) { return reinterpret_cast<float *>(base + o); };
+    auto D = [&](size_t o) { return reinterpret_cast<double *>(base + o); };
+    float *P = F(oP), *Q = F(oQ);
+    // p = W^T (sigma .* x); q = W (d .* p) without the final sign
+    hh_status hs = fused_apply(p, HH_MODE_WT, S, lds, P, n, batch, st);
+    if (hs == HH_OK) {
+        const unsigned fill =
+            (unsigned)std::min<int64_t>(((int64_t)bn / 4 + 255) / 256, (int64_t)p->num_sms * 8);
+        scale_cols_kernel<<<fill, 256, 0, st>>>(P, Q, (const float *)p->d, batch, n);
+        e = cudaGetLastError();
+    }
+    if (hs == HH_OK && e == cudaSuccess) {
+        Plan unsigned_plan = *p;
+        unsigned_plan.sign = nullptr;
+        hs = fused_apply(&unsigned_plan, HH_MODE_W, Q, n, Q, n, batch, st);
+    }
+    const float *sign = (const float *)p->sign;
+    if (hs == HH_OK && e == cudaSuccess) {
+        kern<<<nparts, G, 0, st>>>(gY, ldg, gX, ldgx, batch, n, (const float *)p->u,
+                                   (const float *)p->tau_t, p->ldv, h, sign, (const float *)p->d,
+                                   (const float *)p->gram, Q, P, F(oGd), F(oAW), F(oBW), F(oAT),
+                                   F(oBT), F(odd), vec_ok);
+        e = cudaGetLastError();
+    }
+    if (hs == HH_OK && e == cudaSuccess && gU) {
+        XtyArgs xa{};
+        xa.X[0] = gY, xa.ldx[0] = ldg, xa.Y[0] = F(oAW);
+        xa.X[1] = Q, xa.ldx[1] = n, xa.Y[1] = F(oBW);
+        xa.X[2] = F(oGd), xa.ldx[2] = n, xa.Y[2] = F(oAT);
+        xa.X[3] = P, xa.ldx[3] = n, xa.Y[3] = F(oBT);
+        xa.npairs = 4;
+        xa.post0 = sign;
+        xa.rows = batch;
+        xa.chunk = chunk;
+        xa.n = n;
+        xa.h = h;
+        xa.out = F(oPp);
+        xty_kernel<<<dim3(jt, kt, nchunks), 64, 0, st>>>(xa);
+        // -M[k][j] = sum (-beta_j) alpha_k: X = -beta, Y = alpha, "n" = h; the
+        // two walks' partials one after the other (nchunks x h x h each)
+        for (int w = 0; w < 2; ++w) {
+            XtyArgs xm{};
+            xm.X[0] = F(w ? oBT : oBW), xm.ldx[0] = h, xm.Y[0] = F(w ? oAT : oAW);
+            xm.npairs = 1;
+            xm.rows = batch;
+            xm.chunk = chunk;
+            xm.n = h;
+            xm.h = h;
+            xm.out = F(oMp) + (size_t)w * nchunks * h * h;
+            xty_kernel<<<dim3((h + kXtyJ - 1) / kXtyJ, kt, nchunks), 64, 0, st>>>(xm);
+        }
+        const int64_t hn = (int64_t)h * n, hh = (int64_t)h * h;
+        sum_parts_kernel<<<(unsigned)((hn + 31) / 32), 256, 0, st>>>(F(oPp), nchunks, hn, hn, D(oPst));
+        for (int w = 0; w < 2; ++w)
+            sum_parts_kernel<<<(unsigned)((hh + 31) / 32), 256, 0, st>>>(
+                F(oMp) + (size_t)w * nchunks * h * h, nchunks, hh, hh, D(oM) + (size_t)w * h * h);
+        e = cudaGetLastError();
+    }
+    if (hs == HH_OK && e == cudaSuccess && gd) {
+        sum_parts_kernel<<<(unsigned)((n + 31) / 32), 256, 0, st>>>(F(odd), nparts, C::COVER, n,
+                                                                    D(odd64));
+        e = cudaGetLastError();
+    }
+    if (hs == HH_OK && e == cudaSuccess && (gU || gd)) {
+        combine_kernel<<<dim3(h + 1, (n + 255) / 256), 256, (size_t)h * sizeof(double), st>>>(
+            D(oPst), D(oM), D(oM) + (size_t)h * h, p->tau, (const float *)p->u, p->ldv, n, h, gU,
+            D(odd64), gd);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(base, st);
+    if (e == cudaSuccess) e = e2;
+    if (hs != HH_OK) return hs;
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint (mode S) launch");
+    return HH_OK;
+}
+
 struct PairArgs {
     const int64_t *ia = nullptr, *ib = nullptr;
     int64_t nrows = 0;
@@ -805,8 +1332,8 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
     // a caller's scratch (no allocation allowed), the kernel recomputes.  (For
     // mode 3 the gathered differences would cost more HBM traffic than the
     // recompute saves.)
-    constexpr size_t kPreMaxBytes = size_t(2) << 30;
-    const size_t pre_bytes = (size_t)batch * n * sizeof(T) * 2;
+    constexpr size_t kPreMaxBytes = size_t(3) << 30;
+    const size_t pre_bytes = (size_t)batch * n * sizeof(T) * 3;
     const bool pre = std::is_same<T, float>::value && !scratch && batch > 0 && n % 4 == 0 &&
                      mode == HH_MODE_SYM && pre_bytes <= kPreMaxBytes;
     auto launch = [&](auto kern, size_t smem, bool with_pre) -> hh_status {
@@ -895,6 +1422,11 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
         case HH_MODE_WT: HH_BWD_KERN(HH_MODE_WT, false, BB)
         case HH_MODE_SYM:
             if constexpr (std::is_same<T, float>::value) {
+#if HH_BWD_SYM_CONTRACT
+                if (pre && vec_ok && h % 4 == 0 && h <= 64)
+                    return sym_contract<G, NG, RT, BB>(p, S, lds, gY, ldg, gX, ldgx, gU, gd, batch,
+                                                       vec_ok, st);
+#endif
                 if (pre) HH_BWD_KERN(HH_MODE_SYM, true, BB)
             }
             HH_BWD_KERN(HH_MODE_SYM, false, 1)

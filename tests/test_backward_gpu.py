@@ -58,7 +58,8 @@ def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None):
 
 @pytest.mark.parametrize("mode", ["W", "WT", "SYM"])
 @pytest.mark.parametrize("n,h,B", [(7, 3, 5), (64, 8, 33), (100, 5, 70), (256, 16, 129),
-                                   (1000, 12, 40), (1024, 32, 65), (2048, 6, 9), (4096, 16, 17)])
+                                   (512, 7, 11), (1000, 12, 40), (1024, 32, 65), (1024, 33, 19),
+                                   (2048, 6, 9), (4096, 16, 17)])
 def test_backward_f32(mode, n, h, B):
     _case(mode, n, h, B, torch.float32, seed=n + h)
 
@@ -74,6 +75,14 @@ def test_backward_no_sign_and_zero_reflector():
     for mode in ("W", "WT", "SYM"):
         _, gU = _case(mode, 128, 5, 21, torch.float64, with_sign=False, zero_row=2)
         assert float(gU[2].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("n,h", [(128, 5), (1024, 9)])
+def test_backward_f32_no_sign_and_zero_reflector(n, h):
+    # a zero reflector (tau = 0) gets an exactly zero gradient on every path
+    for mode in ("W", "WT", "SYM"):
+        _, gU = _case(mode, n, h, 23, torch.float32, seed=n + 1, with_sign=False, zero_row=3)
+        assert float(gU[3].abs().max()) == 0.0
 
 
 def test_backward_deterministic():
