@@ -34,6 +34,10 @@
 #ifndef HH_BWD_SYM_CONTRACT
 #define HH_BWD_SYM_CONTRACT 1
 #endif
+// The Mahalanobis gradient in F32 the same way (1) or per tile (0).
+#ifndef HH_BWD_MAHA_CONTRACT
+#define HH_BWD_MAHA_CONTRACT 1
+#endif
 
 // Rows per thread of the F32 adjoint for 128 < n <= 512 (and the default of the
 // compile-time shape overrides below).
@@ -813,16 +817,17 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// One walk round without accumulation: as backward_round, then the rows'
-// alpha and -beta of the round's reflectors go to Aout, Bout (batch x h).
-template <int G, int NG, int RT, int BB, bool DESC>
+// One walk round without accumulation: as backward_round, then for each
+// row r of the tile below the batch end and each reflector k of the round,
+// store(r, k, alpha, beta) (called by thread r).
+template <int G, int NG, int RT, int BB, bool DESC, typename Store>
 __device__ __forceinline__ void walk_round(float (&a)[RT][BCfg<float, G, NG, RT>::E],
                                            float (&g)[RT][BCfg<float, G, NG, RT>::E],
                                            const float *__restrict__ V, int64_t ldv, int k0,
                                            const float *__restrict__ tau,
-                                           const float *__restrict__ gram, float *Aout,
-                                           float *Bout, int64_t r0, int64_t batch, int h, int t,
-                                           int lane, int warp, float *red, int &buf) {
+                                           const float *__restrict__ gram, Store &store,
+                                           int64_t r0, int64_t batch, int t, int lane, int warp,
+                                           float *red, int &buf) {
     using C = BCfg<float, G, NG, RT>;
     constexpr int VEC = C::VEC;
     constexpr int NVB = 2 * BB * RT;
@@ -877,15 +882,12 @@ __device__ __forceinline__ void walk_round(float (&a)[RT][BCfg<float, G, NG, RT>
             }
         }
     }
-    // thread r writes row r's values (every thread holds all of them)
+    // thread r stores row r's values (every thread holds all of them)
 #pragma unroll
     for (int r = 0; r < RT; ++r)
         if (t == r && r0 + r < batch)
 #pragma unroll
-            for (int i = 0; i < BB; ++i) {
-                Aout[(size_t)(r0 + r) * h + kk(i)] = al[i][r];
-                Bout[(size_t)(r0 + r) * h + kk(i)] = -be[i][r];
-            }
+            for (int i = 0; i < BB; ++i) store(r, kk(i), al[i][r], be[i][r]);
 #pragma unroll
     for (int ig = 0; ig < NG; ++ig) {
         float vv[BB][VEC];
@@ -908,21 +910,21 @@ __device__ __forceinline__ void walk_round(float (&a)[RT][BCfg<float, G, NG, RT>
 }
 
 // A whole walk (k = 0 .. h-1, or h-1 .. 0 with DESC) in rounds of BB.
-template <int G, int NG, int RT, int BB, bool DESC>
+template <int G, int NG, int RT, int BB, bool DESC, typename Store>
 __device__ __forceinline__ void walk_all(float (&a)[RT][BCfg<float, G, NG, RT>::E],
                                          float (&g)[RT][BCfg<float, G, NG, RT>::E],
                                          const float *__restrict__ V, int64_t ldv, int h,
                                          const float *__restrict__ tau,
-                                         const float *__restrict__ gram, float *Aout, float *Bout,
-                                         int64_t r0, int64_t batch, int t, int lane, int warp,
-                                         float *red, int &buf) {
+                                         const float *__restrict__ gram, Store &&store, int64_t r0,
+                                         int64_t batch, int t, int lane, int warp, float *red,
+                                         int &buf) {
     int k = DESC ? h - 1 : 0, left = h;
     for (; left >= BB; left -= BB, k += DESC ? -BB : BB)
-        walk_round<G, NG, RT, BB, DESC>(a, g, V, ldv, k, tau, gram, Aout, Bout, r0, batch, h, t,
-                                        lane, warp, red, buf);
+        walk_round<G, NG, RT, BB, DESC>(a, g, V, ldv, k, tau, gram, store, r0, batch, t, lane,
+                                        warp, red, buf);
     for (; left > 0; --left, k += DESC ? -1 : 1)
-        walk_round<G, NG, RT, 1, DESC>(a, g, V, ldv, k, tau, gram, Aout, Bout, r0, batch, h, t,
-                                       lane, warp, red, buf);
+        walk_round<G, NG, RT, 1, DESC>(a, g, V, ldv, k, tau, gram, store, r0, batch, t, lane, warp,
+                                       red, buf);
 }
 
 // The two walks of the mode-S adjoint from the precomputed states Q = W (d .* p)
@@ -962,8 +964,13 @@ sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t b
 #pragma unroll
                 for (int e = 0; e < E; ++e) g[r][e] *= s1[e];
         }
-        walk_all<G, NG, RT, BB, false>(a, g, V, ldv, h, tau, gram, AW, BW, r0, batch, t, lane, warp,
-                                       red, buf);
+        walk_all<G, NG, RT, BB, false>(
+            a, g, V, ldv, h, tau, gram,
+            [&](int r, int k, float al, float be) {
+                AW[(size_t)(r0 + r) * h + k] = al;
+                BW[(size_t)(r0 + r) * h + k] = -be;
+            },
+            r0, batch, t, lane, warp, red, buf);
         load_rows<float, G, NG, RT>(a, P, n, r0, batch, n, t, 1);
         {
             float dv[E];
@@ -989,8 +996,13 @@ sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t b
                 if (col + VEC <= n) fused::store_granule<float>(Gd + row * n + col, q);
             }
         }
-        walk_all<G, NG, RT, BB, true>(a, g, V, ldv, h, tau, gram, AT, BT, r0, batch, t, lane, warp,
-                                      red, buf);
+        walk_all<G, NG, RT, BB, true>(
+            a, g, V, ldv, h, tau, gram,
+            [&](int r, int k, float al, float be) {
+                AT[(size_t)(r0 + r) * h + k] = al;
+                BT[(size_t)(r0 + r) * h + k] = -be;
+            },
+            r0, batch, t, lane, warp, red, buf);
         if (gX) {
             float s1[E];
             if (sign) load_cols<float, G, NG, RT>(s1, sign, t);
@@ -1156,14 +1168,15 @@ sum_parts_kernel(const float *__restrict__ in, int nparts, int64_t stride, int64
 }
 
 // dL/dv_k (row k of gU) = tau_k P_k - tau_k^2 s_k v_k with
-// P_k = Pst[k] + sum_i Cf[k][i] v_i, where for each walk (MW: k = 0 .. h-1
-// first to last; MT: k = h-1 .. 0; the arrays hold -M, M[k][i] = sum_rows
-// alpha_k beta_i)
+// P_k = R1[k] .* dscale + R2[k] + sum_i Cf[k][i] v_i (dscale, R2 optional),
+// where for each walk given (MW: k = 0 .. h-1 first to last; MT: k = h-1 .. 0;
+// the arrays hold -M, M[k][i] = sum_rows alpha_k beta_i)
 //     Cf[k][i] += -tau_i M[k][i] [i walked before k] + tau_i M[i][k] [i walked up to k]
 // and s_k = MW[k][k] + MT[k][k].  Block (h, *) writes dL/dd.  Grid (h + 1,
 // column blocks of 256).
 __global__ void __launch_bounds__(256)
-combine_kernel(const double *__restrict__ Pst, const double *__restrict__ MW,
+combine_kernel(const double *__restrict__ R1, const float *__restrict__ dscale,
+               const double *__restrict__ R2, const double *__restrict__ MW,
                const double *__restrict__ MT, const double *__restrict__ tau,
                const float *__restrict__ V, int64_t ldv, int n, int h, float *gU,
                const double *__restrict__ dd, float *gd) {
@@ -1177,17 +1190,18 @@ combine_kernel(const double *__restrict__ Pst, const double *__restrict__ MW,
     extern __shared__ double cf[];  // h coefficients
     for (int i = threadIdx.x; i < h; i += blockDim.x) {
         double c = 0.0;
-        if (i < k) c += tau[i] * MW[(size_t)k * h + i];
-        if (i <= k) c -= tau[i] * MW[(size_t)i * h + k];
-        if (i > k) c += tau[i] * MT[(size_t)k * h + i];
-        if (i >= k) c -= tau[i] * MT[(size_t)i * h + k];
+        if (MW && i < k) c += tau[i] * MW[(size_t)k * h + i];
+        if (MW && i <= k) c -= tau[i] * MW[(size_t)i * h + k];
+        if (MT && i > k) c += tau[i] * MT[(size_t)k * h + i];
+        if (MT && i >= k) c -= tau[i] * MT[(size_t)i * h + k];
         cf[i] = c;
     }
     __syncthreads();
     if (j >= n) return;
     const double tk = tau[k];
-    const double sk = -(MW[(size_t)k * h + k] + MT[(size_t)k * h + k]);
-    double pk = Pst[(size_t)k * n + j];
+    const double sk = -((MW ? MW[(size_t)k * h + k] : 0.0) + (MT ? MT[(size_t)k * h + k] : 0.0));
+    double pk = R1[(size_t)k * n + j] * (dscale ? (double)dscale[j] : 1.0);
+    if (R2) pk += R2[(size_t)k * n + j];
     for (int i = 0; i < h; ++i) pk += cf[i] * (double)V[(size_t)i * ldv + j];
     gU[(size_t)k * n + j] = (float)(tk * pk - tk * tk * sk * (double)V[(size_t)k * ldv + j]);
 }
@@ -1294,14 +1308,181 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
     }
     if (hs == HH_OK && e == cudaSuccess && (gU || gd)) {
         combine_kernel<<<dim3(h + 1, (n + 255) / 256), 256, (size_t)h * sizeof(double), st>>>(
-            D(oPst), D(oM), D(oM) + (size_t)h * h, p->tau, (const float *)p->u, p->ldv, n, h, gU,
-            D(odd64), gd);
+            D(oPst), nullptr, nullptr, D(oM), D(oM) + (size_t)h * h, p->tau, (const float *)p->u,
+            p->ldv, n, h, gU, D(odd64), gd);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaFreeAsync(base, st);
     if (e == cudaSuccess) e = e2;
     if (hs != HH_OK) return hs;
     if (e != cudaSuccess) return cuda_fail(e, "adjoint (mode S) launch");
+    return HH_OK;
+}
+
+// The Mahalanobis gradient (mode 3) in the same form: per pair the kernel
+// recomputes z = W^T (sigma .* (x_a - x_b)) (forward rounds of FB), stores it
+// to Z, seeds g = 2 g_p d .* z, adds g_p z .* z to its dL/dd partial, and
+// walks back (rounds of BB), storing Y[p] = [2 g_p alpha | -beta] (2h values)
+// and alpha (h values) to Al.  With the walk's start state (z, 2 g_p d .* z),
+//     P_k = d .* (Z^T (2 g_p alpha_k)) - Z^T beta_k + (reflector terms),
+// so one contraction Z^T Y gives both parts.  An index outside [0, nrows)
+// gives a zero row and sets *err, as in the recomputing kernel.
+template <int G, int NG, int RT, int FB, int BB>
+__global__ void __launch_bounds__(G)
+maha_walk_kernel(const float *X, int64_t ldx, int64_t nrows, const int64_t *__restrict__ ia,
+                 const int64_t *__restrict__ ib, const float *__restrict__ gp, int64_t npairs,
+                 int n, const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv,
+                 int h, const float *__restrict__ sign, const float *__restrict__ d,
+                 const float *__restrict__ gram, float *__restrict__ Z, float *__restrict__ Y,
+                 float *__restrict__ Al, float *__restrict__ ddpart, int *__restrict__ err,
+                 int vec_ok) {
+    using C = BCfg<float, G, NG, RT>;
+    constexpr int E = C::E, VEC = C::VEC, COVER = C::COVER;
+    constexpr int NVA = 2 * BB * RT > C::NV ? 2 * BB * RT : C::NV;
+    constexpr int NVMAX = NVA > FB * RT ? NVA : FB * RT;
+    __shared__ float red[2 * NVMAX * C::NW];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    float dd[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) dd[e] = 0.f;
+    int buf = 0;
+    const int64_t tiles = (npairs + RT - 1) / RT;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t r0 = tile * RT;
+        float a[RT][E], g[RT][E];
+        load_pair_rows<float, G, NG, RT>(a, X, ldx, nrows, ia, ib, r0, npairs, n, t, vec_ok, err);
+        if (sign) {
+            float s1[E];
+            load_cols<float, G, NG, RT>(s1, sign, t);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+#pragma unroll
+                for (int e = 0; e < E; ++e) a[r][e] *= s1[e];
+        }
+        forward_walk<float, G, NG, RT, FB>(a, V, ldv, h, tau, gram, t, lane, warp, red, buf);
+        float gw[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) gw[r] = r0 + r < npairs ? gp[r0 + r] : 0.f;
+        {
+            float dv[E];
+            load_cols<float, G, NG, RT>(dv, d, t);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const int64_t row = r0 + r;
+#pragma unroll
+                for (int i = 0; i < NG; ++i) {
+                    const int col = (t + G * i) * VEC;
+                    float q[VEC];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) q[e] = a[r][i * VEC + e];
+                    if (row < npairs && col + VEC <= n)
+                        fused::store_granule<float>(Z + row * n + col, q);
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    dd[e] = fmaf(gw[r] * a[r][e], a[r][e], dd[e]);
+                    g[r][e] = 2.f * gw[r] * dv[e] * a[r][e];
+                }
+            }
+        }
+        walk_all<G, NG, RT, BB, true>(
+            a, g, V, ldv, h, tau, gram,
+            [&](int r, int k, float al, float be) {
+                const size_t row = (size_t)(r0 + r);
+                Y[row * 2 * h + k] = 2.f * gw[r] * al;
+                Y[row * 2 * h + h + k] = -be;
+                Al[row * h + k] = al;
+            },
+            r0, npairs, t, lane, warp, red, buf);
+    }
+    float *dst = ddpart + (size_t)blockIdx.x * COVER;
+#pragma unroll
+    for (int i = 0; i < NG; ++i)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) dst[(size_t)(t + G * i) * VEC + e] = dd[i * VEC + e];
+}
+
+// Mode 3, F32, aligned point rows, n % 4 == 0, h % 4 == 0, h <= 64, bounded
+// work arrays: maha_walk_kernel, the contractions Z^T Y and -M = (-beta)^T
+// alpha, combine_kernel with R1 = rows 0..h-1 scaled by d and R2 = rows
+// h..2h-1.
+template <int G, int NG, int RT, int FB, int BB>
+hh_status maha_contract(const Plan *p, const float *X, int64_t ldx, int64_t nrows,
+                        const int64_t *ia, const int64_t *ib, const float *gout, int64_t npairs,
+                        float *gU, float *gd, int vec_ok, cudaStream_t st) {
+    using C = BCfg<float, G, NG, RT>;
+    const int h = (int)p->h, n = (int)p->n;
+    auto kern = maha_walk_kernel<G, NG, RT, FB, BB>;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, G, 0) != cudaSuccess || nb < 1) nb = 1;
+    const int64_t tiles = (npairs + RT - 1) / RT;
+    const int nparts = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)p->num_sms * nb));
+    const int h2 = 2 * h;
+    const int jt = (n + kXtyJ - 1) / kXtyJ, kt = (h2 + kXtyK - 1) / kXtyK;
+    const int64_t want = std::max<int64_t>(1, (int64_t)p->num_sms * 8 / (jt * kt));
+    int64_t chunk = std::max<int64_t>(256, (npairs + want - 1) / want);
+    chunk = (chunk + kXtySlab - 1) / kXtySlab * kXtySlab;
+    const int nchunks = (int)((npairs + chunk - 1) / chunk);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t oZ = take((size_t)npairs * n * 4), oY = take((size_t)npairs * h2 * 4),
+                 oAl = take((size_t)npairs * h * 4);
+    const size_t odd = take((size_t)nparts * C::COVER * 4);
+    const size_t oRp = take((size_t)nchunks * h2 * n * 4), oMp = take((size_t)nchunks * h * h * 4);
+    const size_t oR = take((size_t)h2 * n * 8), oM = take((size_t)h * h * 8),
+                 odd64 = take((size_t)n * 8);
+    char *base = nullptr;
+    cudaError_t e = dev_malloc_async(reinterpret_cast<void **>(&base), off, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (gradient work arrays)");
+    auto F = [&](size_t o) { return reinterpret_cast<float *>(base + o); };
+    auto D = [&](size_t o) { return reinterpret_cast<double *>(base + o); };
+    kern<<<nparts, G, 0, st>>>(X, ldx, nrows, ia, ib, gout, npairs, n, (const float *)p->u,
+                               (const float *)p->tau_t, p->ldv, h, (const float *)p->sign,
+                               (const float *)p->d, (const float *)p->gram, F(oZ), F(oY), F(oAl),
+                               F(odd), p->err, vec_ok);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && gU) {
+        XtyArgs xa{};
+        xa.X[0] = F(oZ), xa.ldx[0] = n, xa.Y[0] = F(oY);
+        xa.npairs = 1;
+        xa.rows = npairs;
+        xa.chunk = chunk;
+        xa.n = n;
+        xa.h = h2;
+        xa.out = F(oRp);
+        xty_kernel<<<dim3(jt, kt, nchunks), 64, 0, st>>>(xa);
+        XtyArgs xm{};
+        xm.X[0] = F(oY) + h, xm.ldx[0] = h2, xm.Y[0] = F(oAl);
+        xm.npairs = 1;
+        xm.rows = npairs;
+        xm.chunk = chunk;
+        xm.n = h;
+        xm.h = h;
+        xm.out = F(oMp);
+        xty_kernel<<<dim3((h + kXtyJ - 1) / kXtyJ, (h + kXtyK - 1) / kXtyK, nchunks), 64, 0, st>>>(xm);
+        const int64_t rn = (int64_t)h2 * n, hh = (int64_t)h * h;
+        sum_parts_kernel<<<(unsigned)((rn + 31) / 32), 256, 0, st>>>(F(oRp), nchunks, rn, rn, D(oR));
+        sum_parts_kernel<<<(unsigned)((hh + 31) / 32), 256, 0, st>>>(F(oMp), nchunks, hh, hh, D(oM));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && gd) {
+        sum_parts_kernel<<<(unsigned)((n + 31) / 32), 256, 0, st>>>(F(odd), nparts, C::COVER, n,
+                                                                    D(odd64));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && (gU || gd)) {
+        combine_kernel<<<dim3(h + 1, (n + 255) / 256), 256, (size_t)h * sizeof(double), st>>>(
+            D(oR), (const float *)p->d, D(oR) + (size_t)h * n, nullptr, D(oM), p->tau,
+            (const float *)p->u, p->ldv, n, h, gU, D(odd64), gd);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(base, st);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return cuda_fail(e, "Mahalanobis gradient launch");
     return HH_OK;
 }
 
@@ -1430,7 +1611,17 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
                 if (pre) HH_BWD_KERN(HH_MODE_SYM, true, BB)
             }
             HH_BWD_KERN(HH_MODE_SYM, false, 1)
-        default: HH_BWD_KERN(kModeMahalanobis, false, BB)
+        default:
+#if HH_BWD_MAHA_CONTRACT
+            if constexpr (std::is_same<T, float>::value) {
+                const size_t work = (size_t)batch * (n + 3 * h) * sizeof(float);
+                if (!scratch && vec_ok && n % 4 == 0 && h % 4 == 0 && h <= 64 && batch > 0 &&
+                    work <= kPreMaxBytes)
+                    return maha_contract<G, NG, RT, FB, BB>(p, S, lds, pa.nrows, pa.ia, pa.ib, gY,
+                                                            batch, gU, gd, vec_ok, st);
+            }
+#endif
+            HH_BWD_KERN(kModeMahalanobis, false, BB)
     }
 #undef HH_BWD_KERN
 }

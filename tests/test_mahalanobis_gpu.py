@@ -56,7 +56,7 @@ def test_mahalanobis_forward(dtype, n, h):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("n,h", [(256, 16), (100, 7), (1024, 8)])
+@pytest.mark.parametrize("n,h", [(256, 16), (100, 7), (1024, 8), (512, 12), (256, 5)])
 def test_mahalanobis_gradient(dtype, n, h):
     plan, Xg, iag, ibg, U, d, s, X, ia, ib = _setup(n, h, 200, 777, dtype, seed=3 * n + h)
     g = np.random.default_rng(n).standard_normal(ia.shape[0])
@@ -87,12 +87,13 @@ def test_mahalanobis_bad_index_reported():
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-def test_mahalanobis_gradient_bad_index_reported(dtype):
+@pytest.mark.parametrize("h", [5, 8])
+def test_mahalanobis_gradient_bad_index_reported(dtype, h):
     """An out-of-range index in the gradient call is reported, and its pair
     contributes nothing: the gradients equal those of the valid pairs alone."""
     from paper_1811_07624_gb300 import HHError
 
-    plan, Xg, iag, ibg, U, d, s, X, ia, ib = _setup(64, 5, 40, 30, dtype, seed=9)
+    plan, Xg, iag, ibg, U, d, s, X, ia, ib = _setup(64, h, 40, 30, dtype, seed=9)
     g = torch.ones(ia.shape[0], dtype=dtype, device=DEV)
     bad_a, bad_b = iag.clone(), ibg.clone()
     bad_a[3], bad_b[7] = 40, -1
