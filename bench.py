@@ -411,7 +411,8 @@ class MahalanobisRow:
         self.out = torch.empty(self.P, device=dev)
         self.gout = torch.ones(self.P, device=dev) / self.P
         self.torch = torch
-        self.launches = 2 if grad else 1
+        # gradient: the walk, two batch contractions, three fixed-order sums, the combine
+        self.launches = 7 if grad else 1
         self.bound = "alu" if grad else "hbm"
 
     def vectors(self):
@@ -497,7 +498,9 @@ class AdjointRow:
         self.G = torch.randn(self.B, self.n, device=dev, generator=g)
         self.Y = torch.empty_like(self.X)
         self.torch = torch
-        self.launches = 3  # forward, adjoint, fixed-order reduction
+        # forward S x; the adjoint: W^T, d-scaling and W forward states, the two walks,
+        # three batch contractions, four fixed-order sums, the combine
+        self.launches = 13
         self.bound = "alu"
 
     def vectors(self):

@@ -47,13 +47,6 @@ struct WYPlan {
 
 namespace wy {
 
-// L2 policy of the copies: 0 none; 1 GEMM 1's X boxes evict-last, the
-// epilogue's second read of X and the Y stores evict-first (a line is dead
-// after them); 2 only the epilogue's read and the Y stores evict-first.
-#ifndef HH_WY_L2HINT
-#define HH_WY_L2HINT 0
-#endif
-
 constexpr int kTileM = 128;     // rows per tile (M of both GEMMs)
 constexpr int kChunkN = 64;     // output columns per GEMM 2 accumulator
 constexpr int kNumAcc = 2;      // GEMM 2 accumulators, tensor-memory columns 384 + 64a
@@ -299,12 +292,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                 last[s] = it;
                 unsigned char *st = ring + s * stage_bytes;
                 tc::mbar_expect_tx(&B.full[s], bytesX + bytesV);
-#if HH_WY_L2HINT == 1
-                tc::tma_load_2d_hint(st, &mapX, kc * 64, (int)(tile * kTileM), &B.full[s],
-                                     tc::policy_evict_last());
-#else
                 tc::tma_load_2d(st, &mapX, kc * 64, (int)(tile * kTileM), &B.full[s]);
-#endif
                 tc::tma_load_2d(st + bytesX, &mapV, kc * 64, ybase, &B.full[s]);
                 ++it;
             };
@@ -347,13 +335,8 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                     if (aborted()) break;
                     last[e] = ei;
                     tc::mbar_expect_tx(&B.efull[e], kEBox);
-#if HH_WY_L2HINT >= 1
-                    tc::tma_load_2d_hint(ering + e * kEBox, &mapX, (NC - 1 - j) * kChunkN,
-                                         (int)(tile * kTileM), &B.efull[e], tc::policy_evict_first());
-#else
                     tc::tma_load_2d(ering + e * kEBox, &mapX, (NC - 1 - j) * kChunkN,
                                     (int)(tile * kTileM), &B.efull[e]);
-#endif
                 }
             for (int e = 0; e < NE; ++e)
                 if (last[e] != kNone) tc::mbar_wait(&B.efull[e], (last[e] / NE) & 1);
@@ -493,12 +476,7 @@ wy_panel_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant_
                 tc::fence_proxy_async();           // y visible to the TMA store
                 tc::named_barrier(1, 128);         // the four epilogue warps
                 if (leader) {
-#if HH_WY_L2HINT >= 1
-                    tc::tma_store_2d_hint(&mapY, ering + e * kEBox, col0, row0,
-                                          tc::policy_evict_first());
-#else
                     tc::tma_store_2d(&mapY, ering + e * kEBox, col0, row0);
-#endif
                     tc::bulk_commit_group();
                     // the previous box's store has read shared memory: its stage is free
                     tc::bulk_wait_read<1>();
