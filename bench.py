@@ -498,9 +498,9 @@ class AdjointRow:
         self.G = torch.randn(self.B, self.n, device=dev, generator=g)
         self.Y = torch.empty_like(self.X)
         self.torch = torch
-        # forward S x; the adjoint: W^T, d-scaling and W forward states, the two walks,
+        # forward S x; the adjoint from (x, y): the W^T forward state, the two walks,
         # three batch contractions, four fixed-order sums, the combine
-        self.launches = 13
+        self.launches = 11
         self.bound = "alu"
 
     def vectors(self):
@@ -516,14 +516,16 @@ class AdjointRow:
 
     def run(self):
         self.plan.apply_sym(self.X, out=self.Y)
-        self.res = self.plan.backward("SYM", self.X, self.G)
+        self.res = self.plan.backward("SYM", self.X, self.G, Y=self.Y)
 
     def parity(self):
         import oracle
 
         t = self.torch
         sub = 64
-        gX, gU, gd = self.plan.backward("SYM", self.X[:sub].contiguous(), self.G[:sub].contiguous())
+        Ysub = self.plan.apply_sym(self.X[:sub].contiguous())
+        gX, gU, gd = self.plan.backward("SYM", self.X[:sub].contiguous(), self.G[:sub].contiguous(),
+                                        Y=Ysub)
         U32 = t.tensor(self.U, dtype=t.float32).double().numpy()
         d32 = t.tensor(self.d, dtype=t.float32).double().numpy()
         rX, rU, rd = oracle.backward("SYM", U32, self.X[:sub].double().cpu().numpy(),
@@ -543,7 +545,7 @@ class AdjointRow:
 
         def comp():
             self.plan.apply_sym(Xd, out=Yd)
-            _, res["gU"], _ = self.plan.backward("SYM", Xd, Gd, need_gX=False)
+            _, res["gU"], _ = self.plan.backward("SYM", Xd, Gd, need_gX=False, Y=Yd)
 
         def d2h():
             res["gU"].record_stream(torch.cuda.current_stream())

@@ -174,6 +174,20 @@ hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t l
                       void *gd, int64_t batch, void *stream);
 
 /*
+ * hh_backward for mode SYM given the forward output as well: x (the forward
+ * input, batch x n, ldx) and y = S_bar x (batch x n, ldy) as hh_apply_sym of
+ * this plan returned it for the same rows (Eq. (21)).  The state
+ * q = W (d .* W^T (sigma .* x)) that the adjoint walks from is sigma .* y, so
+ * it is read instead of recomputed.  Same gradients, results and errors as
+ * hh_backward(HH_MODE_SYM, x, ...); a y that is not this plan's output for x
+ * gives wrong gradients, not an error.  F32 and F64 plans (F64 and rows that
+ * are not 16-byte aligned take the hh_backward path and do not read y).
+ */
+hh_status hh_backward_sym_y(hh_plan_t plan, const void *x, int64_t ldx, const void *y,
+                            int64_t ldy, const void *gY, int64_t ldgy, void *gX, int64_t ldgx,
+                            void *gU, void *gd, int64_t batch, void *stream);
+
+/*
  * hh_backward that allocates nothing.  The paper has no counterpart: this
  * entry point is for callers that cannot let a library allocate device memory
  * on its own schedule, such as code running inside a host (a framework, a

@@ -168,12 +168,15 @@ class Plan:
 
     # -- backward -----------------------------------------------------------------
     def backward(self, mode: str, saved, gY, need_gX: bool = True, need_gU: bool = True,
-                 need_gd: bool | None = None, stream=None):
+                 need_gd: bool | None = None, stream=None, Y=None):
         """Gradients of L with dL/dY = gY through ``apply_mode(mode, X)``.
 
         saved: the forward output Y for modes "W" and "WT", the forward input X
-        for "SYM".  Returns (gX, gU, gd); gU (h, n) is the gradient with respect
-        to the reflector rows exactly as passed to the plan; gd (n,) only for SYM.
+        for "SYM".  For "SYM", Y may give the forward output as well
+        (``apply_sym(X)`` of this plan): the adjoint then reads its state from
+        it instead of recomputing it (hh_backward_sym_y).  Returns (gX, gU, gd);
+        gU (h, n) is the gradient with respect to the reflector rows exactly as
+        passed to the plan; gd (n,) only for SYM.
         """
         m = _lib.MODES[mode]
         sp, lds = _rows(saved, "saved", self.n, self.dtype)
@@ -188,9 +191,17 @@ class Plan:
             need_gd = mode == "SYM"
         gd = torch.empty((self.n,), device=dev, dtype=self.dtype) if need_gd and mode == "SYM" else None
         xp, ldgx = (None, self.n) if gX is None else _rows(gX, "gX", self.n, self.dtype)
-        _lib.call("hh_backward", self._h, m, sp, lds, gp, ldg, xp, ldgx,
-                  None if gU is None else gU.data_ptr(), None if gd is None else gd.data_ptr(),
-                  B, _stream_ptr(stream))
+        up = None if gU is None else gU.data_ptr()
+        dp = None if gd is None else gd.data_ptr()
+        if Y is not None and mode == "SYM":
+            yp, ldy = _rows(Y, "Y", self.n, self.dtype)
+            if Y.shape[0] != B:
+                raise ValueError("Y and saved must have the same number of rows")
+            _lib.call("hh_backward_sym_y", self._h, sp, lds, yp, ldy, gp, ldg, xp, ldgx, up, dp,
+                      B, _stream_ptr(stream))
+        else:
+            _lib.call("hh_backward", self._h, m, sp, lds, gp, ldg, xp, ldgx, up, dp, B,
+                      _stream_ptr(stream))
         if need_gU and self.h == 0:
             gU = torch.zeros((0, self.n), device=dev, dtype=self.dtype)
         return gX, gU, gd

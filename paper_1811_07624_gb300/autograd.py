@@ -3,7 +3,8 @@
 ``apply(X, U, d, sign, mode)`` is a ``torch.autograd.Function``: the forward
 runs the library's apply kernel, the backward its adjoint kernel
 (``hh_backward``), which recomputes the chain's intermediate vectors from the
-saved output (modes "W", "WT") or input ("SYM") instead of storing them.
+saved output (modes "W", "WT") or input and output ("SYM",
+``hh_backward_sym_y``) instead of storing them.
 Gradients flow to X, to the reflector rows U (as given, unnormalised) and to
 the spectrum d.
 """
@@ -32,16 +33,22 @@ class _ChainFunction(torch.autograd.Function):
         ctx.plan = plan
         ctx.generation = plan.generation
         ctx.mode = mode
-        ctx.save_for_backward(X if mode == "SYM" else Y)
+        # SYM keeps the input and the output: the adjoint reads its state from the
+        # output instead of recomputing it (hh_backward_sym_y)
+        if mode == "SYM":
+            ctx.save_for_backward(X, Y)
+        else:
+            ctx.save_for_backward(Y)
         return Y
 
     @staticmethod
     def backward(ctx, gY):
         _check_generation(ctx)
-        (saved,) = ctx.saved_tensors
+        saved = ctx.saved_tensors
         need_x, need_u, need_d = ctx.needs_input_grad[:3]
-        gX, gU, gd = ctx.plan.backward(ctx.mode, saved, gY.contiguous(), need_gX=need_x,
-                                       need_gU=need_u, need_gd=need_d and ctx.mode == "SYM")
+        gX, gU, gd = ctx.plan.backward(ctx.mode, saved[0], gY.contiguous(), need_gX=need_x,
+                                       need_gU=need_u, need_gd=need_d and ctx.mode == "SYM",
+                                       Y=saved[1] if ctx.mode == "SYM" else None)
         return gX, gU, gd, None, None
 
 

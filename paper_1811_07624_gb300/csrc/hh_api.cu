@@ -352,6 +352,21 @@ hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t l
                     reinterpret_cast<cudaStream_t>(stream));
 }
 
+hh_status hh_backward_sym_y(hh_plan_t plan, const void *x, int64_t ldx, const void *y,
+                            int64_t ldy, const void *gY, int64_t ldgy, void *gX, int64_t ldgx,
+                            void *gU, void *gd, int64_t batch, void *stream) {
+    TraceRange trace("hh_backward_sym_y");
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st =
+        check_backward_args(p, HH_MODE_SYM, x, ldx, gY, ldgy, gX, ldgx, gU, gd, batch);
+    if (st) return st;
+    if ((st = check_rows(p, y, ldy, batch, "y"))) return st;
+    if (gX && gX == y) return fail(HH_ERR_INVALID_ARG, "backward: gX may not alias y");
+    if (batch == 0 && !gU && !gd) return HH_OK;
+    return backward_sym_y(p, x, ldx, y, ldy, gY, ldgy, gX, ldgx, gU, gd, batch,
+                          reinterpret_cast<cudaStream_t>(stream));
+}
+
 static hh_status check_pairs(const Plan *p, const void *X, int64_t ldx, int64_t nrows,
                              const int64_t *ia, const int64_t *ib, int64_t npairs) {
     hh_status st = check_plan(p);

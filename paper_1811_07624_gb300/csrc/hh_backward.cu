@@ -927,8 +927,9 @@ __device__ __forceinline__ void walk_all(float (&a)[RT][BCfg<float, G, NG, RT>::
                                        red, buf);
 }
 
-// The two walks of the mode-S adjoint from the precomputed states Q = W (d .* p)
-// (before the final sign) and P = p: the W walk from (Q, sigma .* dL/dy), then
+// The two walks of the mode-S adjoint from the states q = W (d .* p) (before
+// the final sign: rows of Qsrc, times qsign when given, i.e. sigma .* y for
+// the forward output y) and P = p: the W walk from (q, sigma .* dL/dy), then
 // dL/dd += p .* g, g = d .* g (written to Gd: the second walk's start), the
 // W^T walk from (P, Gd), and dL/dx = sigma .* g.  Per CTA the dL/dd partial
 // (COVER values) goes to ddpart.
@@ -937,8 +938,9 @@ __global__ void __launch_bounds__(G)
 sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t batch, int n,
                 const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv, int h,
                 const float *__restrict__ sign, const float *__restrict__ d,
-                const float *__restrict__ gram, const float *__restrict__ Q,
-                const float *__restrict__ P, float *__restrict__ Gd, float *__restrict__ AW,
+                const float *__restrict__ gram, const float *__restrict__ Qsrc, int64_t ldq,
+                int qvec, const float *__restrict__ qsign, const float *__restrict__ P,
+                float *__restrict__ Gd, float *__restrict__ AW,
                 float *__restrict__ BW, float *__restrict__ AT, float *__restrict__ BT,
                 float *__restrict__ ddpart, int vec_ok) {
     using C = BCfg<float, G, NG, RT>;
@@ -955,14 +957,17 @@ sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t b
         const int64_t r0 = tile * RT;
         float a[RT][E], g[RT][E];
         load_rows<float, G, NG, RT>(g, gY, ldg, r0, batch, n, t, vec_ok);
-        load_rows<float, G, NG, RT>(a, Q, n, r0, batch, n, t, 1);
+        load_rows<float, G, NG, RT>(a, Qsrc, ldq, r0, batch, n, t, qvec);
         if (sign) {
             float s1[E];
             load_cols<float, G, NG, RT>(s1, sign, t);
 #pragma unroll
             for (int r = 0; r < RT; ++r)
 #pragma unroll
-                for (int e = 0; e < E; ++e) g[r][e] *= s1[e];
+                for (int e = 0; e < E; ++e) {
+                    g[r][e] *= s1[e];
+                    if (qsign) a[r][e] *= s1[e];
+                }
         }
         walk_all<G, NG, RT, BB, false>(
             a, g, V, ldv, h, tau, gram,
@@ -1037,7 +1042,8 @@ sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t b
 }
 
 // Batch contraction out[c][k][j] = sum_pairs sum_{rows in chunk c} X[row][j] Y[row][k]
-// (j < n, k < h), the sum of pair 0 scaled by post0[j] when given.  X row-major
+// (j < n, k < h), the sum of the first post_pairs pairs scaled by post0[j]
+// when given.  X row-major
 // with 16-byte aligned rows (n % 4 == 0), Y row-major batch x h (h % 4 == 0).
 // A CTA of 64 threads computes a 128 x 32 (j x k) tile of one chunk, 8 x 8 per
 // thread in FP32 registers, over slabs of 16 rows moved into shared memory by
@@ -1048,6 +1054,7 @@ struct XtyArgs {
     const float *Y[4];
     int npairs;
     const float *post0;
+    int post_pairs;
     int64_t rows, chunk;
     int n, h;
     float *out;  // nchunks x h x n
@@ -1112,7 +1119,7 @@ xty_kernel(const __grid_constant__ XtyArgs args) {
         cp_async_commit();
         cp_async_wait<kXtyStages - 1>();
         __syncthreads();
-        if (s == nsl && args.post0) post_scale();
+        if (s == nsl * args.post_pairs && args.post0) post_scale();
         const int stg = (int)(s % kXtyStages);
 #pragma unroll
         for (int q = 0; q < kXtySlab; ++q) {
@@ -1131,7 +1138,7 @@ xty_kernel(const __grid_constant__ XtyArgs args) {
         __syncthreads();
     }
     cp_async_wait<0>();
-    if (args.npairs == 1 && args.post0) post_scale();
+    if (args.npairs == args.post_pairs && args.post0) post_scale();
     float *o = args.out + (size_t)blockIdx.z * h * n;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -1207,12 +1214,13 @@ combine_kernel(const double *__restrict__ R1, const float *__restrict__ dscale,
 }
 
 // Mode S, F32, allocating path, aligned dL/dy rows, h % 4 == 0, h <= 64:
-// forward states by the fused kernels, the walks by sym_walk_kernel, P_k by
-// the batch contraction, combine_kernel.
+// forward states by the fused kernels (q = sigma .* Ys when the forward
+// output Ys is given, aligned), the walks by sym_walk_kernel, P_k by the
+// batch contraction, combine_kernel.
 template <int G, int NG, int RT, int BB>
 hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *gY, int64_t ldg,
                        float *gX, int64_t ldgx, float *gU, float *gd, int64_t batch, int vec_ok,
-                       cudaStream_t st) {
+                       const float *Ys, int64_t ldy, cudaStream_t st) {
     using C = BCfg<float, G, NG, RT>;
     const int h = (int)p->h, n = (int)p->n;
     const size_t bn = (size_t)batch * n, bh = (size_t)batch * h;
@@ -1233,7 +1241,7 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    const size_t oP = take(bn * 4), oQ = take(bn * 4), oGd = take(bn * 4);
+    const size_t oP = take(bn * 4), oQ = Ys ? 0 : take(bn * 4), oGd = take(bn * 4);
     const size_t oAW = take(bh * 4), oBW = take(bh * 4), oAT = take(bh * 4), oBT = take(bh * 4);
     const size_t odd = take((size_t)nparts * C::COVER * 4);
     const size_t oPp = take((size_t)nchunks * h * n * 4);
@@ -1248,33 +1256,38 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
     float *P = F(oP), *Q = F(oQ);
     // p = W^T (sigma .* x); q = W (d .* p) without the final sign
     hh_status hs = fused_apply(p, HH_MODE_WT, S, lds, P, n, batch, st);
-    if (hs == HH_OK) {
+    if (hs == HH_OK && !Ys) {
         const unsigned fill =
             (unsigned)std::min<int64_t>(((int64_t)bn / 4 + 255) / 256, (int64_t)p->num_sms * 8);
         scale_cols_kernel<<<fill, 256, 0, st>>>(P, Q, (const float *)p->d, batch, n);
         e = cudaGetLastError();
-    }
-    if (hs == HH_OK && e == cudaSuccess) {
-        Plan unsigned_plan = *p;
-        unsigned_plan.sign = nullptr;
-        hs = fused_apply(&unsigned_plan, HH_MODE_W, Q, n, Q, n, batch, st);
+        if (e == cudaSuccess) {
+            Plan unsigned_plan = *p;
+            unsigned_plan.sign = nullptr;
+            hs = fused_apply(&unsigned_plan, HH_MODE_W, Q, n, Q, n, batch, st);
+        }
     }
     const float *sign = (const float *)p->sign;
+    // q = sigma .* y (Ys given) or the recomputed state (Q)
+    const float *qsrc = Ys ? Ys : Q;
+    const int64_t ldq = Ys ? ldy : n;
     if (hs == HH_OK && e == cudaSuccess) {
         kern<<<nparts, G, 0, st>>>(gY, ldg, gX, ldgx, batch, n, (const float *)p->u,
                                    (const float *)p->tau_t, p->ldv, h, sign, (const float *)p->d,
-                                   (const float *)p->gram, Q, P, F(oGd), F(oAW), F(oBW), F(oAT),
-                                   F(oBT), F(odd), vec_ok);
+                                   (const float *)p->gram, qsrc, ldq, 1, Ys ? sign : nullptr, P,
+                                   F(oGd), F(oAW), F(oBW), F(oAT), F(oBT), F(odd), vec_ok);
         e = cudaGetLastError();
     }
     if (hs == HH_OK && e == cudaSuccess && gU) {
         XtyArgs xa{};
         xa.X[0] = gY, xa.ldx[0] = ldg, xa.Y[0] = F(oAW);
-        xa.X[1] = Q, xa.ldx[1] = n, xa.Y[1] = F(oBW);
+        xa.X[1] = qsrc, xa.ldx[1] = ldq, xa.Y[1] = F(oBW);
         xa.X[2] = F(oGd), xa.ldx[2] = n, xa.Y[2] = F(oAT);
         xa.X[3] = P, xa.ldx[3] = n, xa.Y[3] = F(oBT);
         xa.npairs = 4;
+        // sigma scales (sigma .* dL/dy)^T alpha, and (sigma .* y)^T beta when q = sigma .* y
         xa.post0 = sign;
+        xa.post_pairs = Ys ? 2 : 1;
         xa.rows = batch;
         xa.chunk = chunk;
         xa.n = n;
@@ -1489,6 +1502,8 @@ hh_status maha_contract(const Plan *p, const float *X, int64_t ldx, int64_t nrow
 struct PairArgs {
     const int64_t *ia = nullptr, *ib = nullptr;
     int64_t nrows = 0;
+    const void *ysym = nullptr;  // mode S: the forward output y = S_bar x, or null
+    int64_t ldy = 0;
 };
 
 template <typename T, int G, int NG, int RT, int MINB = 1, int BB = 1, int FB = 1>
@@ -1604,9 +1619,12 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
         case HH_MODE_SYM:
             if constexpr (std::is_same<T, float>::value) {
 #if HH_BWD_SYM_CONTRACT
-                if (pre && vec_ok && h % 4 == 0 && h <= 64)
-                    return sym_contract<G, NG, RT, BB>(p, S, lds, gY, ldg, gX, ldgx, gU, gd, batch,
-                                                       vec_ok, st);
+                if (pre && vec_ok && h % 4 == 0 && h <= 64) {
+                    const bool yok = pa.ysym && (uintptr_t)pa.ysym % 16 == 0 && pa.ldy % 4 == 0;
+                    return sym_contract<G, NG, RT, BB>(
+                        p, S, lds, gY, ldg, gX, ldgx, gU, gd, batch, vec_ok,
+                        yok ? (const float *)pa.ysym : nullptr, yok ? pa.ldy : 0, st);
+                }
 #endif
                 if (pre) HH_BWD_KERN(HH_MODE_SYM, true, BB)
             }
@@ -1706,6 +1724,21 @@ hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, cons
     if (p->dtype == HH_F64)
         return bwd::dispatch<double>(p, mode, S, lds, gY, ldg, gX, ldgx, gU, gd, batch, scratch,
                                      scratch_bytes, pa, st);
+    return fail(HH_ERR_UNSUPPORTED, "backward: F32 and F64 plans only");
+}
+
+hh_status backward_sym_y(const Plan *p, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                         const void *gY, int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd,
+                         int64_t batch, cudaStream_t st) {
+    bwd::PairArgs pa;
+    pa.ysym = Y;
+    pa.ldy = ldy;
+    if (p->dtype == HH_F32)
+        return bwd::dispatch<float>(p, HH_MODE_SYM, X, ldx, gY, ldg, gX, ldgx, gU, gd, batch,
+                                    nullptr, 0, pa, st);
+    if (p->dtype == HH_F64)
+        return bwd::dispatch<double>(p, HH_MODE_SYM, X, ldx, gY, ldg, gX, ldgx, gU, gd, batch,
+                                     nullptr, 0, pa, st);
     return fail(HH_ERR_UNSUPPORTED, "backward: F32 and F64 plans only");
 }
 

@@ -150,6 +150,10 @@ hh_status check_backward_args(const Plan *p, hh_mode mode, const void *saved, in
 hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
                    int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
                    void *scratch, size_t scratch_bytes, cudaStream_t st);
+// Mode SYM with the forward output y = S_bar x (q = sigma .* y is read).
+hh_status backward_sym_y(const Plan *p, const void *X, int64_t ldx, const void *Y, int64_t ldy,
+                         const void *gY, int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd,
+                         int64_t batch, cudaStream_t st);
 
 // ---- fast Mahalanobis distance (hh_mahalanobis.cu, hh_backward.cu) ----
 hh_status mahalanobis(const Plan *p, const void *X, int64_t ldx, int64_t nrows, const int64_t *ia,

@@ -24,7 +24,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None):
+def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None, with_y=False):
     from paper_1811_07624_gb300 import Plan
 
     U = si.reflectors(n, h, seed=seed, unit=False)
@@ -41,7 +41,7 @@ def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None):
     Gg = torch.as_tensor(G, dtype=dtype, device=DEV)
     Y = plan.apply_mode(mode, Xg)
     saved = Xg if mode == "SYM" else Y
-    gX, gU, gd = plan.backward(mode, saved, Gg)
+    gX, gU, gd = plan.backward(mode, saved, Gg, Y=Y if with_y else None)
     plan.sync()
     as64 = lambda t: t.double().cpu().numpy()  # noqa: E731
     rX, rU, rd = oracle.backward(mode, as64(Ut), as64(Xg), as64(Gg), sign=s, d=as64(dt))
@@ -62,6 +62,18 @@ def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None):
                                    (2048, 6, 9), (4096, 16, 17)])
 def test_backward_f32(mode, n, h, B):
     _case(mode, n, h, B, torch.float32, seed=n + h)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,h,B", [(7, 3, 5), (256, 16, 129), (1024, 32, 65), (1024, 33, 19),
+                                   (4096, 16, 17)])
+def test_backward_sym_with_forward_output(dtype, n, h, B):
+    # hh_backward_sym_y: the state sigma .* y read from the forward output (F64
+    # adjoints stop at n = 2048, as in hh_backward)
+    if dtype == torch.float64 and n > 2048:
+        pytest.skip("F64 adjoint limit")
+    _case("SYM", n, h, B, dtype, seed=n + 2 * h, with_y=True)
+    _case("SYM", n, h, B, dtype, seed=n + 2 * h, with_y=True, with_sign=False)
 
 
 @pytest.mark.parametrize("mode", ["W", "WT", "SYM"])

@@ -142,6 +142,13 @@ def test_adjoint_sym_full_size():
         rd += cd
     assert _rel(gU.double().cpu().numpy(), rU) <= 1e-4
     assert _rel(gd.double().cpu().numpy(), rd) <= 1e-4
+    # with the forward output (the state read from y instead of recomputed)
+    Y = plan.apply_sym(X)
+    gXy, gUy, gdy = plan.backward("SYM", X, G, Y=Y)
+    plan.sync()
+    assert _rel(gXy[idx].double().cpu().numpy(), rX) <= 1e-4
+    assert _rel(gUy.double().cpu().numpy(), rU) <= 1e-4
+    assert _rel(gdy.double().cpu().numpy(), rd) <= 1e-4
     plan.close()
 
 
