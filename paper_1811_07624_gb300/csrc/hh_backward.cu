@@ -799,9 +799,9 @@ scale_cols_kernel(const float *__restrict__ P, float *__restrict__ Q, const floa
 //     P_k = G^T alpha_k - A^T beta_k - sum_{j before k} tau_j M[k][j] v_j
 //           + sum_{j up to k} tau_j M[j][k] v_j,        M = alpha^T beta (h x h).
 // The walk kernel writes each row's alpha_k and -beta_k and the state G of the
-// second walk; G^T alpha - A^T beta and M are batch contractions (xty_kernel,
-// FP32 within a chunk of rows, FP64 across chunks in a fixed order), and
-// combine_kernel forms
+// second walk; G^T alpha - A^T beta and M are batch contractions (xty_kernel
+// and mm_small_kernel, FP32 within a chunk of rows, FP64 across chunks in a
+// fixed order), and combine_kernel forms
 // dL/dv_k = tau_k P_k - tau_k^2 s_k v_k with s_k = M[k][k].  The same
 // quantities as the per-tile accumulation, summed in a different order.
 
@@ -1152,6 +1152,50 @@ xty_kernel(const __grid_constant__ XtyArgs args) {
     }
 }
 
+// Small contraction out[b][k * h + j] = sum over the rows of block b of
+// X[row][j] * Y[row][k] (j, k < h <= 64; X, Y row-major with leading
+// dimensions ldx, ldy): 64-row slabs staged in shared memory, each thread
+// accumulating its h^2 / 256 outputs in FP32.  Block b covers rows
+// [b * chunk, (b + 1) * chunk).
+constexpr int kMmRows = 64;
+__global__ void __launch_bounds__(256)
+mm_small_kernel(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Y, int64_t ldy,
+                int64_t rows, int64_t chunk, int h, float *__restrict__ out) {
+    __shared__ float xs[kMmRows][64], ys[kMmRows][64];
+    const int t = threadIdx.x;
+    const int64_t rb = (int64_t)blockIdx.x * chunk;
+    const int64_t re = min(rows, rb + chunk);
+    const int hh = h * h;
+    float acc[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) acc[m] = 0.f;
+    for (int64_t r = rb; r < re; r += kMmRows) {
+        for (int i = t; i < kMmRows * h; i += 256) {
+            const int rr = i / h, c = i - rr * h;
+            const int64_t row = r + rr;
+            xs[rr][c] = row < re ? X[row * ldx + c] : 0.f;
+            ys[rr][c] = row < re ? Y[row * ldy + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int q = t + 256 * m;
+            if (q < hh) {
+                const int k = q / h, j = q - k * h;
+                float a = acc[m];
+                for (int rr = 0; rr < kMmRows; ++rr) a = fmaf(xs[rr][j], ys[rr][k], a);
+                acc[m] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int q = t + 256 * m;
+        if (q < hh) out[(size_t)blockIdx.x * hh + q] = acc[m];
+    }
+}
+
 // out[i] = sum over p of in[p * stride + i] in FP64 (i < count), p increasing
 // within each of 8 interleaved groups, the groups added in order.  Block b
 // handles i in [32b, 32b + 32).
@@ -1244,8 +1288,11 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
     const size_t oP = take(bn * 4), oQ = Ys ? 0 : take(bn * 4), oGd = take(bn * 4);
     const size_t oAW = take(bh * 4), oBW = take(bh * 4), oAT = take(bh * 4), oBT = take(bh * 4);
     const size_t odd = take((size_t)nparts * C::COVER * 4);
+    // the h x h contraction: blocks of mchunk rows, two per SM
+    const int64_t mchunk = std::max<int64_t>(kMmRows, (batch + 2 * p->num_sms - 1) / (2 * p->num_sms));
+    const int nmm = (int)((batch + mchunk - 1) / mchunk);
     const size_t oPp = take((size_t)nchunks * h * n * 4);
-    const size_t oMp = take((size_t)nchunks * 2 * h * h * 4);
+    const size_t oMp = take((size_t)nmm * 2 * h * h * 4);
     const size_t oPst = take((size_t)h * n * 8), oM = take((size_t)2 * h * h * 8),
                  odd64 = take((size_t)n * 8);
     char *base = nullptr;
@@ -1294,24 +1341,16 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
         xa.h = h;
         xa.out = F(oPp);
         xty_kernel<<<dim3(jt, kt, nchunks), 64, 0, st>>>(xa);
-        // -M[k][j] = sum (-beta_j) alpha_k: X = -beta, Y = alpha, "n" = h; the
-        // two walks' partials one after the other (nchunks x h x h each)
-        for (int w = 0; w < 2; ++w) {
-            XtyArgs xm{};
-            xm.X[0] = F(w ? oBT : oBW), xm.ldx[0] = h, xm.Y[0] = F(w ? oAT : oAW);
-            xm.npairs = 1;
-            xm.rows = batch;
-            xm.chunk = chunk;
-            xm.n = h;
-            xm.h = h;
-            xm.out = F(oMp) + (size_t)w * nchunks * h * h;
-            xty_kernel<<<dim3((h + kXtyJ - 1) / kXtyJ, kt, nchunks), 64, 0, st>>>(xm);
-        }
+        // -M[k][j] = sum (-beta_j) alpha_k: X = -beta, Y = alpha; the two walks'
+        // partials one after the other (nmm x h x h each)
+        for (int w = 0; w < 2; ++w)
+            mm_small_kernel<<<nmm, 256, 0, st>>>(F(w ? oBT : oBW), h, F(w ? oAT : oAW), h, batch,
+                                                 mchunk, h, F(oMp) + (size_t)w * nmm * h * h);
         const int64_t hn = (int64_t)h * n, hh = (int64_t)h * h;
         sum_parts_kernel<<<(unsigned)((hn + 31) / 32), 256, 0, st>>>(F(oPp), nchunks, hn, hn, D(oPst));
         for (int w = 0; w < 2; ++w)
             sum_parts_kernel<<<(unsigned)((hh + 31) / 32), 256, 0, st>>>(
-                F(oMp) + (size_t)w * nchunks * h * h, nchunks, hh, hh, D(oM) + (size_t)w * h * h);
+                F(oMp) + (size_t)w * nmm * h * h, nmm, hh, hh, D(oM) + (size_t)w * h * h);
         e = cudaGetLastError();
     }
     if (hs == HH_OK && e == cudaSuccess && gd) {
@@ -1445,7 +1484,10 @@ hh_status maha_contract(const Plan *p, const float *X, int64_t ldx, int64_t nrow
     const size_t oZ = take((size_t)npairs * n * 4), oY = take((size_t)npairs * h2 * 4),
                  oAl = take((size_t)npairs * h * 4);
     const size_t odd = take((size_t)nparts * C::COVER * 4);
-    const size_t oRp = take((size_t)nchunks * h2 * n * 4), oMp = take((size_t)nchunks * h * h * 4);
+    const int64_t mchunk =
+        std::max<int64_t>(kMmRows, (npairs + 2 * p->num_sms - 1) / (2 * p->num_sms));
+    const int nmm = (int)((npairs + mchunk - 1) / mchunk);
+    const size_t oRp = take((size_t)nchunks * h2 * n * 4), oMp = take((size_t)nmm * h * h * 4);
     const size_t oR = take((size_t)h2 * n * 8), oM = take((size_t)h * h * 8),
                  odd64 = take((size_t)n * 8);
     char *base = nullptr;
@@ -1468,18 +1510,11 @@ hh_status maha_contract(const Plan *p, const float *X, int64_t ldx, int64_t nrow
         xa.h = h2;
         xa.out = F(oRp);
         xty_kernel<<<dim3(jt, kt, nchunks), 64, 0, st>>>(xa);
-        XtyArgs xm{};
-        xm.X[0] = F(oY) + h, xm.ldx[0] = h2, xm.Y[0] = F(oAl);
-        xm.npairs = 1;
-        xm.rows = npairs;
-        xm.chunk = chunk;
-        xm.n = h;
-        xm.h = h;
-        xm.out = F(oMp);
-        xty_kernel<<<dim3((h + kXtyJ - 1) / kXtyJ, (h + kXtyK - 1) / kXtyK, nchunks), 64, 0, st>>>(xm);
+        // -M[k][j] = sum (-beta_j) alpha_k: X = -beta (columns h.. of Y), Y = alpha
+        mm_small_kernel<<<nmm, 256, 0, st>>>(F(oY) + h, h2, F(oAl), h, npairs, mchunk, h, F(oMp));
         const int64_t rn = (int64_t)h2 * n, hh = (int64_t)h * h;
         sum_parts_kernel<<<(unsigned)((rn + 31) / 32), 256, 0, st>>>(F(oRp), nchunks, rn, rn, D(oR));
-        sum_parts_kernel<<<(unsigned)((hh + 31) / 32), 256, 0, st>>>(F(oMp), nchunks, hh, hh, D(oM));
+        sum_parts_kernel<<<(unsigned)((hh + 31) / 32), 256, 0, st>>>(F(oMp), nmm, hh, hh, D(oM));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && gd) {
