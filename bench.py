@@ -497,10 +497,11 @@ class AdjointRow:
         self.X = torch.randn(self.B, self.n, device=dev, generator=g)
         self.G = torch.randn(self.B, self.n, device=dev, generator=g)
         self.Y = torch.empty_like(self.X)
+        self.P = torch.empty_like(self.X)
         self.torch = torch
-        # forward S x; the adjoint from (x, y): the W^T forward state, the two walks,
-        # three batch contractions, four fixed-order sums, the combine
-        self.launches = 11
+        # forward S x keeping p; the adjoint from (p, y): the two walks, three batch
+        # contractions, four fixed-order sums, the combine
+        self.launches = 10
         self.bound = "alu"
 
     def vectors(self):
@@ -515,17 +516,16 @@ class AdjointRow:
         return float((8 * self.h + 1) * self.n * 5) * self.B
 
     def run(self):
-        self.plan.apply_sym(self.X, out=self.Y)
-        self.res = self.plan.backward("SYM", self.X, self.G, Y=self.Y)
+        self.plan.apply_sym_p(self.X, out=self.Y, p_out=self.P)
+        self.res = self.plan.backward("SYM", None, self.G, Y=self.Y, P=self.P)
 
     def parity(self):
         import oracle
 
         t = self.torch
         sub = 64
-        Ysub = self.plan.apply_sym(self.X[:sub].contiguous())
-        gX, gU, gd = self.plan.backward("SYM", self.X[:sub].contiguous(), self.G[:sub].contiguous(),
-                                        Y=Ysub)
+        Ysub, Psub = self.plan.apply_sym_p(self.X[:sub].contiguous())
+        gX, gU, gd = self.plan.backward("SYM", None, self.G[:sub].contiguous(), Y=Ysub, P=Psub)
         U32 = t.tensor(self.U, dtype=t.float32).double().numpy()
         d32 = t.tensor(self.d, dtype=t.float32).double().numpy()
         rX, rU, rd = oracle.backward("SYM", U32, self.X[:sub].double().cpu().numpy(),
@@ -537,6 +537,7 @@ class AdjointRow:
         Xh, Gh = pinned_copy(torch, self.X), pinned_copy(torch, self.G)
         gUh = torch.empty(self.h, self.n, pin_memory=True)
         Xd, Gd, Yd = torch.empty_like(self.X), torch.empty_like(self.G), torch.empty_like(self.X)
+        Pd = torch.empty_like(self.X)
         res = {}
 
         def h2d():
@@ -544,8 +545,8 @@ class AdjointRow:
             Gd.copy_(Gh, non_blocking=True)
 
         def comp():
-            self.plan.apply_sym(Xd, out=Yd)
-            _, res["gU"], _ = self.plan.backward("SYM", Xd, Gd, need_gX=False, Y=Yd)
+            self.plan.apply_sym_p(Xd, out=Yd, p_out=Pd)
+            _, res["gU"], _ = self.plan.backward("SYM", None, Gd, need_gX=False, Y=Yd, P=Pd)
 
         def d2h():
             res["gU"].record_stream(torch.cuda.current_stream())

@@ -174,6 +174,30 @@ hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t l
                       void *gd, int64_t batch, void *stream);
 
 /*
+ * hh_apply_sym that also writes p = W^T (sigma .* x) (batch x n, leading
+ * dimension ldp), the state between the two halves of Eq. (21), for
+ * hh_backward_sym_py.  Where the column-split kernels run (F32, aligned rows,
+ * 512 < n <= 1024 with h <= 50, or 2048 < n <= 4096 with h <= 25) p is stored
+ * inside the same pass; elsewhere a W^T pass writes it first, so Y may alias
+ * X.  P may alias neither X nor Y.  F32 and F64 plans.
+ */
+hh_status hh_apply_sym_p(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                         void *P, int64_t ldp, int64_t batch, void *stream);
+
+/*
+ * hh_backward for mode SYM from p = W^T (sigma .* x) and y = S_bar x as
+ * hh_apply_sym_p returned them (Eq. (21)); the input x is not needed.  The
+ * adjoint's states are read instead of recomputed (on F32 with aligned rows,
+ * n and h multiples of 4 and h <= 64; otherwise x = sigma .* (W p) is formed
+ * first, W being orthogonal).  Same gradients and errors as
+ * hh_backward(HH_MODE_SYM, x, ...); p and y that are not this plan's for
+ * one x give wrong gradients, not an error.
+ */
+hh_status hh_backward_sym_py(hh_plan_t plan, const void *P, int64_t ldp, const void *y,
+                             int64_t ldy, const void *gY, int64_t ldgy, void *gX, int64_t ldgx,
+                             void *gU, void *gd, int64_t batch, void *stream);
+
+/*
  * hh_backward for mode SYM given the forward output as well: x (the forward
  * input, batch x n, ldx) and y = S_bar x (batch x n, ldy) as hh_apply_sym of
  * this plan returned it for the same rows (Eq. (21)).  The state

@@ -61,6 +61,8 @@ SIGNATURES = {
     "hh_backward": [vp, ip, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
     "hh_backward_noalloc": [vp, ip, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
     "hh_backward_sym_y": [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
+    "hh_backward_sym_py": [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp, i64, vp],
+    "hh_apply_sym_p": [vp, vp, i64, vp, i64, vp, i64, i64, vp],
     "hh_mahalanobis": [vp, vp, i64, i64, vp, vp, i64, vp, vp],
     "hh_mahalanobis_backward": [vp, vp, i64, i64, vp, vp, i64, vp, vp, vp, vp],
     "hh_batch_create": [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(i64)],

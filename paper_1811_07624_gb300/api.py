@@ -163,22 +163,43 @@ class Plan:
         """sigma .* W (d .* W^T (sigma .* x)) per row (Eq. (21))."""
         return self._apply("hh_apply_sym", X, out, stream)
 
+    def apply_sym_p(self, X, out=None, p_out=None, stream=None):
+        """apply_sym that also returns p = W^T (sigma .* x), the state between the
+        halves of Eq. (21), for ``backward("SYM", None, gY, Y=y, P=p)``.  Returns (y, p)."""
+        xp, ldx = _rows(X, "X", self.n, self.dtype)
+        B = X.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n), device=X.device, dtype=self.dtype)
+        if p_out is None:
+            p_out = torch.empty((B, self.n), device=X.device, dtype=self.dtype)
+        yp, ldy = _rows(out, "out", self.n, self.dtype)
+        pp, ldp = _rows(p_out, "p_out", self.n, self.dtype)
+        if out.shape[0] != B or p_out.shape[0] != B:
+            raise ValueError("out and p_out must have as many rows as X")
+        _lib.call("hh_apply_sym_p", self._h, xp, ldx, yp, ldy, pp, ldp, B, _stream_ptr(stream))
+        return out, p_out
+
     def apply_mode(self, mode: str, X, out=None, stream=None):
         return {"W": self.apply, "WT": self.apply_T, "SYM": self.apply_sym}[mode](X, out, stream)
 
     # -- backward -----------------------------------------------------------------
     def backward(self, mode: str, saved, gY, need_gX: bool = True, need_gU: bool = True,
-                 need_gd: bool | None = None, stream=None, Y=None):
+                 need_gd: bool | None = None, stream=None, Y=None, P=None):
         """Gradients of L with dL/dY = gY through ``apply_mode(mode, X)``.
 
         saved: the forward output Y for modes "W" and "WT", the forward input X
         for "SYM".  For "SYM", Y may give the forward output as well
         (``apply_sym(X)`` of this plan): the adjoint then reads its state from
-        it instead of recomputing it (hh_backward_sym_y).  Returns (gX, gU, gd);
-        gU (h, n) is the gradient with respect to the reflector rows exactly as
-        passed to the plan; gd (n,) only for SYM.
+        it instead of recomputing it (hh_backward_sym_y); with Y and P from
+        ``apply_sym_p(X)``, saved may be None (hh_backward_sym_py).  Returns
+        (gX, gU, gd); gU (h, n) is the gradient with respect to the reflector
+        rows exactly as passed to the plan; gd (n,) only for SYM.
         """
         m = _lib.MODES[mode]
+        if mode == "SYM" and P is not None:
+            if Y is None:
+                raise ValueError("P needs Y as well")
+            saved = P
         sp, lds = _rows(saved, "saved", self.n, self.dtype)
         gp, ldg = _rows(gY, "gY", self.n, self.dtype)
         if saved.shape[0] != gY.shape[0]:
@@ -197,8 +218,9 @@ class Plan:
             yp, ldy = _rows(Y, "Y", self.n, self.dtype)
             if Y.shape[0] != B:
                 raise ValueError("Y and saved must have the same number of rows")
-            _lib.call("hh_backward_sym_y", self._h, sp, lds, yp, ldy, gp, ldg, xp, ldgx, up, dp,
-                      B, _stream_ptr(stream))
+            fn = "hh_backward_sym_py" if P is not None else "hh_backward_sym_y"
+            _lib.call(fn, self._h, sp, lds, yp, ldy, gp, ldg, xp, ldgx, up, dp, B,
+                      _stream_ptr(stream))
         else:
             _lib.call("hh_backward", self._h, m, sp, lds, gp, ldg, xp, ldgx, up, dp, B,
                       _stream_ptr(stream))

@@ -3,8 +3,8 @@
 ``apply(X, U, d, sign, mode)`` is a ``torch.autograd.Function``: the forward
 runs the library's apply kernel, the backward its adjoint kernel
 (``hh_backward``), which recomputes the chain's intermediate vectors from the
-saved output (modes "W", "WT") or input and output ("SYM",
-``hh_backward_sym_y``) instead of storing them.
+saved output (modes "W", "WT") or, for "SYM", from p = W^T (sigma .* x) and
+the output kept by the forward (``hh_apply_sym_p``, ``hh_backward_sym_py``).
 Gradients flow to X, to the reflector rows U (as given, unnormalised) and to
 the spectrum d.
 """
@@ -29,15 +29,16 @@ def _check_generation(ctx):
 class _ChainFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, U, d, plan, mode):
-        Y = plan.apply_mode(mode, X.contiguous())
         ctx.plan = plan
         ctx.generation = plan.generation
         ctx.mode = mode
-        # SYM keeps the input and the output: the adjoint reads its state from the
-        # output instead of recomputing it (hh_backward_sym_y)
+        # SYM keeps p = W^T (sigma .* x) and the output: the adjoint reads both
+        # states instead of recomputing them (hh_apply_sym_p, hh_backward_sym_py)
         if mode == "SYM":
-            ctx.save_for_backward(X, Y)
+            Y, P = plan.apply_sym_p(X.contiguous())
+            ctx.save_for_backward(P, Y)
         else:
+            Y = plan.apply_mode(mode, X.contiguous())
             ctx.save_for_backward(Y)
         return Y
 
@@ -46,9 +47,10 @@ class _ChainFunction(torch.autograd.Function):
         _check_generation(ctx)
         saved = ctx.saved_tensors
         need_x, need_u, need_d = ctx.needs_input_grad[:3]
-        gX, gU, gd = ctx.plan.backward(ctx.mode, saved[0], gY.contiguous(), need_gX=need_x,
-                                       need_gU=need_u, need_gd=need_d and ctx.mode == "SYM",
-                                       Y=saved[1] if ctx.mode == "SYM" else None)
+        sym = ctx.mode == "SYM"
+        gX, gU, gd = ctx.plan.backward(ctx.mode, None if sym else saved[0], gY.contiguous(),
+                                       need_gX=need_x, need_gU=need_u, need_gd=need_d and sym,
+                                       Y=saved[1] if sym else None, P=saved[0] if sym else None)
         return gX, gU, gd, None, None
 
 

@@ -352,6 +352,42 @@ hh_status hh_backward(hh_plan_t plan, hh_mode mode, const void *saved, int64_t l
                     reinterpret_cast<cudaStream_t>(stream));
 }
 
+hh_status hh_apply_sym_p(hh_plan_t plan, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                         void *P, int64_t ldp, int64_t batch, void *stream) {
+    TraceRange trace("hh_apply_sym_p");
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st = check_plan(p);
+    if (st) return st;
+    if (p->path != HH_PATH_FUSED)
+        return fail(HH_ERR_UNSUPPORTED, "apply_sym_p: F32 and F64 plans only");
+    if (batch < 0) return fail(HH_ERR_INVALID_ARG, "batch %lld < 0", (long long)batch);
+    if ((st = check_rows(p, X, ldx, batch, "X"))) return st;
+    if ((st = check_rows(p, Y, ldy, batch, "Y"))) return st;
+    if ((st = check_rows(p, P, ldp, batch, "P"))) return st;
+    if (!p->d) return fail(HH_ERR_INVALID_ARG, "apply_sym: the plan has no spectrum d");
+    if (X == Y && ldx != ldy) return fail(HH_ERR_INVALID_ARG, "in-place apply needs ldx == ldy");
+    if (batch > 0 && (P == X || P == Y))
+        return fail(HH_ERR_INVALID_ARG, "apply_sym_p: P may alias neither X nor Y");
+    if (batch == 0) return HH_OK;
+    return fused_apply_p(p, HH_MODE_SYM, X, ldx, Y, ldy, P, ldp, batch,
+                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+hh_status hh_backward_sym_py(hh_plan_t plan, const void *P, int64_t ldp, const void *y,
+                             int64_t ldy, const void *gY, int64_t ldgy, void *gX, int64_t ldgx,
+                             void *gU, void *gd, int64_t batch, void *stream) {
+    TraceRange trace("hh_backward_sym_py");
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    hh_status st =
+        check_backward_args(p, HH_MODE_SYM, P, ldp, gY, ldgy, gX, ldgx, gU, gd, batch);
+    if (st) return st;
+    if ((st = check_rows(p, y, ldy, batch, "y"))) return st;
+    if (gX && gX == y) return fail(HH_ERR_INVALID_ARG, "backward: gX may not alias y");
+    if (batch == 0 && !gU && !gd) return HH_OK;
+    return backward_sym_py(p, P, ldp, y, ldy, gY, ldgy, gX, ldgx, gU, gd, batch,
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
 hh_status hh_backward_sym_y(hh_plan_t plan, const void *x, int64_t ldx, const void *y,
                             int64_t ldy, const void *gY, int64_t ldgy, void *gX, int64_t ldgx,
                             void *gU, void *gd, int64_t batch, void *stream) {

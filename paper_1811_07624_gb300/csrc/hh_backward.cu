@@ -940,7 +940,7 @@ sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t b
                 const float *__restrict__ sign, const float *__restrict__ d,
                 const float *__restrict__ gram, const float *__restrict__ Qsrc, int64_t ldq,
                 int qvec, const float *__restrict__ qsign, const float *__restrict__ P,
-                float *__restrict__ Gd, float *__restrict__ AW,
+                int64_t ldp, float *__restrict__ Gd, float *__restrict__ AW,
                 float *__restrict__ BW, float *__restrict__ AT, float *__restrict__ BT,
                 float *__restrict__ ddpart, int vec_ok) {
     using C = BCfg<float, G, NG, RT>;
@@ -976,7 +976,7 @@ sym_walk_kernel(const float *gY, int64_t ldg, float *gX, int64_t ldgx, int64_t b
                 BW[(size_t)(r0 + r) * h + k] = -be;
             },
             r0, batch, t, lane, warp, red, buf);
-        load_rows<float, G, NG, RT>(a, P, n, r0, batch, n, t, 1);
+        load_rows<float, G, NG, RT>(a, P, ldp, r0, batch, n, t, 1);
         {
             float dv[E];
             load_cols<float, G, NG, RT>(dv, d, t);
@@ -1264,7 +1264,8 @@ combine_kernel(const double *__restrict__ R1, const float *__restrict__ dscale,
 template <int G, int NG, int RT, int BB>
 hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *gY, int64_t ldg,
                        float *gX, int64_t ldgx, float *gU, float *gd, int64_t batch, int vec_ok,
-                       const float *Ys, int64_t ldy, cudaStream_t st) {
+                       const float *Ys, int64_t ldy, const float *Pg, int64_t ldpg,
+                       cudaStream_t st) {
     using C = BCfg<float, G, NG, RT>;
     const int h = (int)p->h, n = (int)p->n;
     const size_t bn = (size_t)batch * n, bh = (size_t)batch * h;
@@ -1285,7 +1286,7 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    const size_t oP = take(bn * 4), oQ = Ys ? 0 : take(bn * 4), oGd = take(bn * 4);
+    const size_t oP = Pg ? 0 : take(bn * 4), oQ = Ys ? 0 : take(bn * 4), oGd = take(bn * 4);
     const size_t oAW = take(bh * 4), oBW = take(bh * 4), oAT = take(bh * 4), oBT = take(bh * 4);
     const size_t odd = take((size_t)nparts * C::COVER * 4);
     // the h x h contraction: blocks of mchunk rows, two per SM
@@ -1300,9 +1301,11 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (adjoint work arrays)");
     auto F = [&](size_t o) { return reinterpret_cast<float *>(base + o); };
     auto D = [&](size_t o) { return reinterpret_cast<double *>(base + o); };
-    float *P = F(oP), *Q = F(oQ);
-    // p = W^T (sigma .* x); q = W (d .* p) without the final sign
-    hh_status hs = fused_apply(p, HH_MODE_WT, S, lds, P, n, batch, st);
+    // p = W^T (sigma .* x) (given as Pg, or computed); q = W (d .* p) without
+    // the final sign (sigma .* Ys when the forward output is given)
+    float *P = Pg ? const_cast<float *>(Pg) : F(oP), *Q = F(oQ);
+    const int64_t ldp = Pg ? ldpg : n;
+    hh_status hs = Pg ? HH_OK : fused_apply(p, HH_MODE_WT, S, lds, P, n, batch, st);
     if (hs == HH_OK && !Ys) {
         const unsigned fill =
             (unsigned)std::min<int64_t>(((int64_t)bn / 4 + 255) / 256, (int64_t)p->num_sms * 8);
@@ -1322,7 +1325,7 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
         kern<<<nparts, G, 0, st>>>(gY, ldg, gX, ldgx, batch, n, (const float *)p->u,
                                    (const float *)p->tau_t, p->ldv, h, sign, (const float *)p->d,
                                    (const float *)p->gram, qsrc, ldq, 1, Ys ? sign : nullptr, P,
-                                   F(oGd), F(oAW), F(oBW), F(oAT), F(oBT), F(odd), vec_ok);
+                                   ldp, F(oGd), F(oAW), F(oBW), F(oAT), F(oBT), F(odd), vec_ok);
         e = cudaGetLastError();
     }
     if (hs == HH_OK && e == cudaSuccess && gU) {
@@ -1330,7 +1333,7 @@ hh_status sym_contract(const Plan *p, const float *S, int64_t lds, const float *
         xa.X[0] = gY, xa.ldx[0] = ldg, xa.Y[0] = F(oAW);
         xa.X[1] = qsrc, xa.ldx[1] = ldq, xa.Y[1] = F(oBW);
         xa.X[2] = F(oGd), xa.ldx[2] = n, xa.Y[2] = F(oAT);
-        xa.X[3] = P, xa.ldx[3] = n, xa.Y[3] = F(oBT);
+        xa.X[3] = P, xa.ldx[3] = ldp, xa.Y[3] = F(oBT);
         xa.npairs = 4;
         // sigma scales (sigma .* dL/dy)^T alpha, and (sigma .* y)^T beta when q = sigma .* y
         xa.post0 = sign;
@@ -1539,6 +1542,8 @@ struct PairArgs {
     int64_t nrows = 0;
     const void *ysym = nullptr;  // mode S: the forward output y = S_bar x, or null
     int64_t ldy = 0;
+    const void *psym = nullptr;  // mode S: p = W^T (sigma .* x), or null (then S is x)
+    int64_t ldp = 0;
 };
 
 template <typename T, int G, int NG, int RT, int MINB = 1, int BB = 1, int FB = 1>
@@ -1658,7 +1663,8 @@ hh_status run(const Plan *p, int mode, const T *S, int64_t lds, const T *gY, int
                     const bool yok = pa.ysym && (uintptr_t)pa.ysym % 16 == 0 && pa.ldy % 4 == 0;
                     return sym_contract<G, NG, RT, BB>(
                         p, S, lds, gY, ldg, gX, ldgx, gU, gd, batch, vec_ok,
-                        yok ? (const float *)pa.ysym : nullptr, yok ? pa.ldy : 0, st);
+                        yok ? (const float *)pa.ysym : nullptr, yok ? pa.ldy : 0,
+                        (const float *)pa.psym, pa.ldp, st);
                 }
 #endif
                 if (pre) HH_BWD_KERN(HH_MODE_SYM, true, BB)
@@ -1775,6 +1781,49 @@ hh_status backward_sym_y(const Plan *p, const void *X, int64_t ldx, const void *
         return bwd::dispatch<double>(p, HH_MODE_SYM, X, ldx, gY, ldg, gX, ldgx, gU, gd, batch,
                                      nullptr, 0, pa, st);
     return fail(HH_ERR_UNSUPPORTED, "backward: F32 and F64 plans only");
+}
+
+hh_status backward_sym_py(const Plan *p, const void *P, int64_t ldp, const void *Y, int64_t ldy,
+                          const void *gY, int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd,
+                          int64_t batch, cudaStream_t st) {
+    const int64_t n = p->n, h = p->h;
+    const auto al = [](const void *q, int64_t ld) { return (uintptr_t)q % 16 == 0 && ld % 4 == 0; };
+    // the contraction path reads p and y directly
+    const bool direct = p->dtype == HH_F32 && batch > 0 && n % 4 == 0 && h % 4 == 0 && h <= 64 &&
+                        (size_t)batch * n * 4 * 3 <= (size_t(3) << 30) && al(P, ldp) &&
+                        al(Y, ldy) && al(gY, ldg) && (!gX || al(gX, ldgx));
+    bwd::PairArgs pa;
+    pa.ysym = Y;
+    pa.ldy = ldy;
+    if (direct) {
+        pa.psym = P;
+        pa.ldp = ldp;
+        return bwd::dispatch<float>(p, HH_MODE_SYM, nullptr, ldp, gY, ldg, gX, ldgx, gU, gd, batch,
+                                    nullptr, 0, pa, st);
+    }
+    // otherwise the input first: x = sigma .* (W p), W orthogonal
+    if (p->dtype != HH_F32 && p->dtype != HH_F64)
+        return fail(HH_ERR_UNSUPPORTED, "backward: F32 and F64 plans only");
+    const size_t es = dtype_size(p->dtype);
+    void *X = nullptr;
+    if (batch > 0) {
+        cudaError_t e = dev_malloc_async(&X, (size_t)batch * n * es, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (backward input)");
+    }
+    hh_status hs = batch > 0 ? fused_apply(p, HH_MODE_W, P, ldp, X, n, batch, st) : HH_OK;
+    if (hs == HH_OK) {
+        if (p->dtype == HH_F32)
+            hs = bwd::dispatch<float>(p, HH_MODE_SYM, X, n, gY, ldg, gX, ldgx, gU, gd, batch,
+                                      nullptr, 0, pa, st);
+        else
+            hs = bwd::dispatch<double>(p, HH_MODE_SYM, X, n, gY, ldg, gX, ldgx, gU, gd, batch,
+                                       nullptr, 0, pa, st);
+    }
+    if (X) {
+        cudaError_t e = cudaFreeAsync(X, st);
+        if (hs == HH_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync (backward input)");
+    }
+    return hs;
 }
 
 hh_status mahalanobis_backward(const Plan *p, const void *X, int64_t ldx, int64_t nrows,

@@ -42,10 +42,49 @@
 
 namespace hh {
 
+// The column-split kernels (which can store p inside the mode-S pass) take
+// these shapes.
+static bool split_shape(int vec_ok, int64_t n, int h, const int *start) {
+    if (!(vec_ok && n % 4 == 0 && n <= 8192)) return false;
+#ifndef HH_NO_SPLIT
+    if (n > 512 && n <= 1024 && !start && h >= 1 && h <= split::max_h<32, 8, 4, 8, 4, 1>())
+        return true;
+    if (n > 2048 && n <= 4096 && !start &&
+        h <= split::max_h<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>())
+        return true;
+#endif
+    return false;
+}
+
+static cudaError_t dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
+                                int64_t batch, int64_t n, const float *U, const float *tau,
+                                int64_t ldv, int h, const float *gram, const float *sign,
+                                const float *d, int vec_ok, int *err, int num_sms, cudaStream_t st,
+                                const int *start, float *P, int64_t ldp);
+
+// P (mode S only, may be null): also write p = W^T (sigma .* x), inside the
+// pass where the split kernels run, else by a W^T pass before it (so that
+// Y may alias X).
 cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                                int64_t batch, int64_t n, const float *U, const float *tau, int64_t ldv, int h,
                                const float *gram, const float *sign, const float *d, int vec_ok,
-                               int *err, int num_sms, cudaStream_t st, const int *start) {
+                               int *err, int num_sms, cudaStream_t st, const int *start, float *P,
+                               int64_t ldp) {
+    if (mode == HH_MODE_SYM && P && !split_shape(vec_ok, n, h, start)) {
+        cudaError_t e = dispatch_f32(HH_MODE_WT, X, ldx, P, ldp, batch, n, U, tau, ldv, h, gram,
+                                     sign, d, vec_ok, err, num_sms, st, start, nullptr, 0);
+        if (e != cudaSuccess) return e;
+        P = nullptr;
+    }
+    return dispatch_f32(mode, X, ldx, Y, ldy, batch, n, U, tau, ldv, h, gram, sign, d, vec_ok, err,
+                        num_sms, st, start, mode == HH_MODE_SYM ? P : nullptr, ldp);
+}
+
+static cudaError_t dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
+                                int64_t batch, int64_t n, const float *U, const float *tau,
+                                int64_t ldv, int h, const float *gram, const float *sign,
+                                const float *d, int vec_ok, int *err, int num_sms, cudaStream_t st,
+                                const int *start, float *P, int64_t ldp) {
     using namespace fused;
     const int ni = (int)n;
     // Aligned rows with n % 4 == 0: persistent blocked kernel, tiles prefetched
@@ -68,9 +107,9 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
             h <= split::max_h<32, 8, 4, 8, 4, 1>()) {
             if (h >= 16)
                 return split::launch<32, 8, 4, 8, 4, 1, 1>(mode, X, ldx, Y, ldy, batch, ni, U, tau,
-                                                           ldv, h, gram, sign, d, err, st);
+                                                           ldv, h, gram, sign, d, err, st, P, ldp);
             return split::launch<32, 8, 4, 8, 2, 1, 1>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv,
-                                                       h, gram, sign, d, err, st);
+                                                       h, gram, sign, d, err, st, P, ldp);
         }
 #endif
         if (n <= 1024) return HH_STAGED(HH_N1024_G, HH_N1024_NG, HH_N1024_RT, HH_N1024_RG, HH_N1024_B);
@@ -79,7 +118,7 @@ cudaError_t fused_dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float 
         if (n > 2048 && n <= 4096 && !start &&
             h <= split::max_h<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>())
             return split::launch<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>(
-                mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, d, err, st);
+                mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, d, err, st, P, ldp);
 #endif
         if (n <= 4096) return HH_STAGED(HH_N4096_G, HH_N4096_NG, HH_N4096_RT, HH_N4096_RG, HH_N4096_B);
         return HH_STAGED(512, 4, 2, 1, 2);

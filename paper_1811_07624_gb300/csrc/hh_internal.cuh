@@ -139,6 +139,10 @@ hh_status wy_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void
 // ---- fused apply (hh_fused.cu) ----
 hh_status fused_apply(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void *Y,
                       int64_t ldy, int64_t batch, cudaStream_t st);
+// The same; mode SYM with P (may be null) also writes p = W^T (sigma .* x)
+// (rows of P, leading dimension ldp).
+hh_status fused_apply_p(const Plan *p, hh_mode mode, const void *X, int64_t ldx, void *Y,
+                        int64_t ldy, void *P, int64_t ldp, int64_t batch, cudaStream_t st);
 
 // ---- adjoint (hh_backward.cu) ----
 // Argument checks shared by the adjoint entry points (hh_api.cu).
@@ -150,6 +154,10 @@ hh_status check_backward_args(const Plan *p, hh_mode mode, const void *saved, in
 hh_status backward(const Plan *p, hh_mode mode, const void *S, int64_t lds, const void *gY,
                    int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd, int64_t batch,
                    void *scratch, size_t scratch_bytes, cudaStream_t st);
+// Mode SYM from p = W^T (sigma .* x) and y = S_bar x (the input is not needed).
+hh_status backward_sym_py(const Plan *p, const void *P, int64_t ldp, const void *Y, int64_t ldy,
+                          const void *gY, int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd,
+                          int64_t batch, cudaStream_t st);
 // Mode SYM with the forward output y = S_bar x (q = sigma .* y is read).
 hh_status backward_sym_y(const Plan *p, const void *X, int64_t ldx, const void *Y, int64_t ldy,
                          const void *gY, int64_t ldg, void *gX, int64_t ldgx, void *gU, void *gd,

@@ -297,12 +297,13 @@ __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2
 // Y rows and bases 16-byte aligned, V rows zero padded to ldv >= 2*HALF,
 // ldv % 4 == 0, h*HALF floats of dynamic shared memory.  Launched as clusters
 // of two CTAs (cluster rank = the half of the columns a CTA owns).
-template <int MODE, int G, int NG, int RT, int RG, int B, int CL, int MINB>
+template <int MODE, int G, int NG, int RT, int RG, int B, int CL, int MINB, bool KP = false>
 __global__ void __launch_bounds__(G *RG, MINB)
 split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t batch, int n,
                    const float *__restrict__ V, const float *__restrict__ tau, int64_t ldv, int h,
                    const float *__restrict__ gram, const float *__restrict__ sign,
-                   const float *__restrict__ d, int *__restrict__ err) {
+                   const float *__restrict__ d, int *__restrict__ err, float *__restrict__ P,
+                   int64_t ldp) {
     using C = XCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NV = C::NV, HALF = C::HALF;
     extern __shared__ __align__(128) float vs[];  // h x HALF: this CTA's half of every reflector
@@ -381,7 +382,24 @@ split_chain_kernel(const float *X, int64_t ldx, float *Y, int64_t ldy, int64_t b
         if (MODE != HH_MODE_W && sign) scale_half<G, NG, RT, RG, B>(x, sign, c0, t);
         // W: k = h..1; W^T: k = 1..h; S: k = 1..h, scale by d, k = h..1
         for (int half = 0; half < (MODE == HH_MODE_SYM ? 2 : 1); ++half) {
-            if (half == 1) scale_half<G, NG, RT, RG, B>(x, d, c0, t);
+            if (half == 1) {
+                // mode S with P (KP): p = W^T (sigma .* x), the state between the halves
+                if constexpr (KP)
+#pragma unroll
+                    for (int r = 0; r < RT; ++r) {
+                        if (r0 + r >= batch) continue;
+                        float *pr = P + (r0 + r) * ldp + c0;
+#pragma unroll
+                        for (int i = 0; i < NG; ++i) {
+                            const int col = (t + G * i) * 4;
+                            if (col < ncols)
+                                __stcs(reinterpret_cast<float4 *>(pr + col),
+                                       make_float4(x[r][2 * i].x, x[r][2 * i].y,
+                                                   x[r][2 * i + 1].x, x[r][2 * i + 1].y));
+                        }
+                    }
+                scale_half<G, NG, RT, RG, B>(x, d, c0, t);
+            }
             const bool asc = MODE != HH_MODE_W && half == 0;
             chain<G, NG, RT, RG, B, CL>(x, asc, h, vs, tau, gram, t, lane, warp, &rslot[rg][0],
                                         &rbar[rg][0], xc, err);
@@ -419,12 +437,13 @@ constexpr int max_h() {
 }
 
 // CL CTAs per cluster split the columns (CTA r owns [r*HALF, (r+1)*HALF));
-// MINB CTAs per SM bound the registers.
+// MINB CTAs per SM bound the registers.  Mode S with P also writes
+// p = W^T (sigma .* x) (rows of P, leading dimension ldp, 16-byte aligned).
 template <int G, int NG, int RT, int RG, int B, int CL = 2, int MINB = 1>
 cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
                    int64_t batch, int n, const float *V, const float *tau, int64_t ldv, int h,
                    const float *gram, const float *sign, const float *d, int *err,
-                   cudaStream_t st) {
+                   cudaStream_t st, float *P = nullptr, int64_t ldp = 0) {
     using C = XCfg<G, NG, RT, RG, B>;
     constexpr size_t kMaxSmem = max_smem<MINB>();
     if (n < 1 || n > CL * C::HALF || n % 4 || ldv < CL * C::HALF || ldv % 4 ||
@@ -433,8 +452,8 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
     const size_t smem = h > 0 ? (size_t)h * C::HALF * sizeof(float) : 16;
     // per kernel (one per mode) and device: the shared-memory opt-in at the
     // largest request, and the co-resident clusters measured with it
-    static PerDevice state[3];
-    auto run = [&](auto kern) -> cudaError_t {
+    static PerDevice state[4];  // W, W^T, S, S keeping p
+    auto run = [&](auto kern, int si) -> cudaError_t {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -446,7 +465,7 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int ncl = 1;
-        cudaError_t e = per_device(state[mode], ncl, [&](int &v) -> cudaError_t {
+        cudaError_t e = per_device(state[si], ncl, [&](int &v) -> cudaError_t {
             cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)kMaxSmem);
             if (e2 != cudaSuccess) return e2;
@@ -465,12 +484,14 @@ cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t 
         cfg.gridDim = dim3(CL * grid_cl);
         cfg.dynamicSmemBytes = smem;
         return cudaLaunchKernelEx(&cfg, kern, X, ldx, Y, ldy, batch, n, V, tau, ldv, h, gram,
-                                  sign, d, err);
+                                  sign, d, err, mode == HH_MODE_SYM ? P : nullptr, ldp);
     };
     switch (mode) {
-        case HH_MODE_W: return run(split_chain_kernel<HH_MODE_W, G, NG, RT, RG, B, CL, MINB>);
-        case HH_MODE_WT: return run(split_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B, CL, MINB>);
-        default: return run(split_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B, CL, MINB>);
+        case HH_MODE_W: return run(split_chain_kernel<HH_MODE_W, G, NG, RT, RG, B, CL, MINB>, 0);
+        case HH_MODE_WT: return run(split_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B, CL, MINB>, 1);
+        default:
+            if (P) return run(split_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B, CL, MINB, true>, 3);
+            return run(split_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B, CL, MINB>, 2);
     }
 }
 

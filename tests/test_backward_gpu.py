@@ -24,7 +24,8 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None, with_y=False):
+def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None, with_y=False,
+          with_p=False):
     from paper_1811_07624_gb300 import Plan
 
     U = si.reflectors(n, h, seed=seed, unit=False)
@@ -41,7 +42,16 @@ def _case(mode, n, h, B, dtype, seed=0, with_sign=True, zero_row=None, with_y=Fa
     Gg = torch.as_tensor(G, dtype=dtype, device=DEV)
     Y = plan.apply_mode(mode, Xg)
     saved = Xg if mode == "SYM" else Y
-    gX, gU, gd = plan.backward(mode, saved, Gg, Y=Y if with_y else None)
+    if with_p:
+        # the forward keeps p = W^T (sigma .* x); y as apply_sym, p as apply_T
+        Yp, P = plan.apply_sym_p(Xg)
+        assert torch.equal(Yp, Y)
+        PT = plan.apply_T(Xg)
+        assert float((P - PT).abs().max()) <= (1e-5 if dtype == torch.float32 else 1e-12) * \
+            float(PT.abs().max())
+        gX, gU, gd = plan.backward(mode, None, Gg, Y=Yp, P=P)
+    else:
+        gX, gU, gd = plan.backward(mode, saved, Gg, Y=Y if with_y else None)
     plan.sync()
     as64 = lambda t: t.double().cpu().numpy()  # noqa: E731
     rX, rU, rd = oracle.backward(mode, as64(Ut), as64(Xg), as64(Gg), sign=s, d=as64(dt))
@@ -74,6 +84,37 @@ def test_backward_sym_with_forward_output(dtype, n, h, B):
         pytest.skip("F64 adjoint limit")
     _case("SYM", n, h, B, dtype, seed=n + 2 * h, with_y=True)
     _case("SYM", n, h, B, dtype, seed=n + 2 * h, with_y=True, with_sign=False)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n,h,B", [(7, 3, 5), (256, 16, 129), (1024, 32, 65), (1024, 33, 19),
+                                   (2048, 8, 9), (4096, 16, 17), (4096, 40, 6)])
+def test_backward_sym_from_p_and_y(dtype, n, h, B):
+    # hh_apply_sym_p keeps p (inside the split kernels' pass at n in (512, 1024],
+    # (2048, 4096] and small h; by a W^T pass elsewhere), hh_backward_sym_py
+    # starts from (p, y) without x
+    if dtype == torch.float64 and n > 2048:
+        pytest.skip("F64 adjoint limit")
+    _case("SYM", n, h, B, dtype, seed=n + 3 * h, with_p=True)
+    _case("SYM", n, h, B, dtype, seed=n + 3 * h, with_p=True, with_sign=False)
+
+
+def test_apply_sym_p_in_place():
+    from paper_1811_07624_gb300 import Plan
+
+    for n, h in ((256, 7), (1024, 16)):
+        g = torch.Generator(device=DEV).manual_seed(n)
+        plan = Plan(torch.randn(h, n, device=DEV, generator=g),
+                    d=torch.rand(n, device=DEV, generator=g) + 0.5)
+        X = torch.randn(33, n, device=DEV, generator=g)
+        Y = plan.apply_sym(X)
+        PT = plan.apply_T(X)
+        Xc = X.clone()
+        Yi, P = plan.apply_sym_p(Xc, out=Xc)  # y over x
+        plan.sync()
+        assert Yi.data_ptr() == Xc.data_ptr()
+        assert torch.equal(Yi, Y)
+        assert float((P - PT).abs().max()) <= 1e-5 * float(PT.abs().max())
 
 
 @pytest.mark.parametrize("mode", ["W", "WT", "SYM"])

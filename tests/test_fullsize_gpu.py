@@ -142,13 +142,17 @@ def test_adjoint_sym_full_size():
         rd += cd
     assert _rel(gU.double().cpu().numpy(), rU) <= 1e-4
     assert _rel(gd.double().cpu().numpy(), rd) <= 1e-4
-    # with the forward output (the state read from y instead of recomputed)
+    # with the forward output (the state read from y instead of recomputed), and
+    # from (p, y) kept by the forward
     Y = plan.apply_sym(X)
     gXy, gUy, gdy = plan.backward("SYM", X, G, Y=Y)
+    Y2, P = plan.apply_sym_p(X)
+    gXp, gUp, gdp = plan.backward("SYM", None, G, Y=Y2, P=P)
     plan.sync()
-    assert _rel(gXy[idx].double().cpu().numpy(), rX) <= 1e-4
-    assert _rel(gUy.double().cpu().numpy(), rU) <= 1e-4
-    assert _rel(gdy.double().cpu().numpy(), rd) <= 1e-4
+    for a, b, c in ((gXy, gUy, gdy), (gXp, gUp, gdp)):
+        assert _rel(a[idx].double().cpu().numpy(), rX) <= 1e-4
+        assert _rel(b.double().cpu().numpy(), rU) <= 1e-4
+        assert _rel(c.double().cpu().numpy(), rd) <= 1e-4
     plan.close()
 
 
