@@ -28,6 +28,12 @@
 #define HH_N4096_B 2
 #endif
 
+// Eight-CTA clusters for 2048 < n <= 4096 beyond the pair's h (1) or the
+// staged kernel there (0).
+#ifndef HH_SPLIT8
+#define HH_SPLIT8 1
+#endif
+
 // Column-split cluster kernel for 2048 < n <= 4096 (each CTA of a pair keeps
 // its 2048 columns of every reflector in shared memory): (G, NG, RT, RG, B).
 // For 512 < n <= 1024 the same kernel runs on single-CTA "clusters" holding
@@ -52,6 +58,9 @@ static bool split_shape(int vec_ok, int64_t n, int h, const int *start) {
     if (n > 2048 && n <= 4096 && !start &&
         h <= split::max_h<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>())
         return true;
+#if HH_SPLIT8
+    if (n > 2048 && n <= 4096 && !start && h <= split::max_h<32, 4, 8, 8, 4>()) return true;
+#endif
 #endif
     return false;
 }
@@ -119,6 +128,13 @@ static cudaError_t dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float
             h <= split::max_h<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>())
             return split::launch<HH_SPLIT_G, HH_SPLIT_NG, HH_SPLIT_RT, HH_SPLIT_RG, HH_SPLIT_B>(
                 mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv, h, gram, sign, d, err, st, P, ldp);
+#if HH_SPLIT8
+        // larger h: clusters of eight CTAs, each keeping 512 columns of every
+        // reflector (32 threads x 16 columns x 8 rows per row group)
+        if (n > 2048 && n <= 4096 && !start && h <= split::max_h<32, 4, 8, 8, 4>())
+            return split::launch<32, 4, 8, 8, 4, 8, 1>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv,
+                                                       h, gram, sign, d, err, st, P, ldp);
+#endif
 #endif
         if (n <= 4096) return HH_STAGED(HH_N4096_G, HH_N4096_NG, HH_N4096_RT, HH_N4096_RG, HH_N4096_B);
         return HH_STAGED(512, 4, 2, 1, 2);

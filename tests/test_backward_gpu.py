@@ -203,3 +203,56 @@ def test_module_trains():
         opt.step()
         losses.append(float(loss.detach()))
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_sym_p_and_y_entry_errors():
+    # argument errors of hh_apply_sym_p, hh_backward_sym_y and hh_backward_sym_py
+    from paper_1811_07624_gb300 import Plan, _lib
+
+    L = _lib.lib()
+    n, B = 64, 5
+    g = torch.Generator(device=DEV).manual_seed(4)
+    plan = Plan(torch.randn(4, n, device=DEV, generator=g),
+                d=torch.rand(n, device=DEV, generator=g) + 0.5)
+    X = torch.randn(B, n, device=DEV, generator=g)
+    Y = torch.empty_like(X)
+    P = torch.empty_like(X)
+    G = torch.randn(B, n, device=DEV, generator=g)
+    gX = torch.empty_like(X)
+
+    def code(st):
+        return _lib.STATUS[st]
+
+    # p may alias neither the input nor the output
+    assert code(L.hh_apply_sym_p(plan.handle, X.data_ptr(), n, Y.data_ptr(), n, X.data_ptr(), n,
+                                 B, None)) == "HH_ERR_INVALID_ARG"
+    assert code(L.hh_apply_sym_p(plan.handle, X.data_ptr(), n, Y.data_ptr(), n, Y.data_ptr(), n,
+                                 B, None)) == "HH_ERR_INVALID_ARG"
+    # a host pointer for P
+    Ph = torch.empty(B, n).pin_memory()
+    assert code(L.hh_apply_sym_p(plan.handle, X.data_ptr(), n, Y.data_ptr(), n, Ph.data_ptr(), n,
+                                 B, None)) == "HH_ERR_INVALID_ARG"
+    assert code(L.hh_apply_sym_p(plan.handle, X.data_ptr(), n, Y.data_ptr(), n, P.data_ptr(), n,
+                                 B, None)) == "HH_OK"
+    # dL/dx may not alias y
+    assert code(L.hh_backward_sym_y(plan.handle, X.data_ptr(), n, Y.data_ptr(), n, G.data_ptr(),
+                                    n, Y.data_ptr(), n, None, None, B, None)) == "HH_ERR_INVALID_ARG"
+    assert code(L.hh_backward_sym_py(plan.handle, P.data_ptr(), n, Y.data_ptr(), n, G.data_ptr(),
+                                     n, Y.data_ptr(), n, None, None, B, None)) == "HH_ERR_INVALID_ARG"
+    # leading dimension below n
+    assert code(L.hh_backward_sym_py(plan.handle, P.data_ptr(), n - 1, Y.data_ptr(), n,
+                                     G.data_ptr(), n, gX.data_ptr(), n, None, None, B,
+                                     None)) == "HH_ERR_INVALID_ARG"
+    # an empty batch is a no-op
+    assert code(L.hh_backward_sym_py(plan.handle, P.data_ptr(), n, Y.data_ptr(), n, G.data_ptr(),
+                                     n, gX.data_ptr(), n, None, None, 0, None)) == "HH_OK"
+    # a plan without a spectrum
+    plain = Plan(torch.randn(4, n, device=DEV, generator=g))
+    assert code(L.hh_apply_sym_p(plain.handle, X.data_ptr(), n, Y.data_ptr(), n, P.data_ptr(), n,
+                                 B, None)) == "HH_ERR_INVALID_ARG"
+    # BF16 (compact-WY) plans have no mode S
+    wy = Plan(torch.randn(64, n, device=DEV, generator=g).bfloat16())
+    Xb = X.bfloat16()
+    assert code(L.hh_apply_sym_p(wy.handle, Xb.data_ptr(), n, Xb.clone().data_ptr(), n,
+                                 Xb.clone().data_ptr(), n, B, None)) == "HH_ERR_UNSUPPORTED"
+    plan.sync()

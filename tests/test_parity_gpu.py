@@ -108,6 +108,14 @@ def test_f32_reflector_counts(h):
         _check(mode, 4096, h, 9, torch.float32, seed=h)
 
 
+@pytest.mark.parametrize("n,h", [(2052, 26), (3000, 40), (4096, 100), (4096, 101)])
+def test_f32_eight_cta_clusters(n, h):
+    # 2048 < n <= 4096 beyond the CTA pair's h: clusters of eight CTAs with 512
+    # columns each (the last ones partly past n) up to h = 100, staged above
+    for mode in ("W", "WT", "SYM"):
+        _check(mode, n, h, 21, torch.float32, seed=n + h)
+
+
 @pytest.mark.parametrize("batch", [0, 1, 2, 7, 8, 9, 31, 33, 513])
 def test_batch_tails(batch):
     for n in (256, 1000, 4096):
