@@ -648,6 +648,8 @@ def fitting_compare(torch, dev, n=128, h=16, seed=0):
     from paper_1811_07624_gb300 import shf
 
     S = si.random_symmetric(n, seed)
+    # warm-up: the first GPU eigendecomposition loads the solver library
+    torch.linalg.eigh(torch.eye(4, device=dev, dtype=torch.float64))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = shf.SHF(torch.tensor(S, device=dev), h)

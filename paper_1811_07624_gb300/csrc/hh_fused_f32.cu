@@ -48,6 +48,24 @@
 
 namespace hh {
 
+// A second stream per device (non-blocking, created on first use), on which
+// a launch can run part of its work beside the caller's stream.
+static cudaError_t side_stream(cudaStream_t &out) {
+    static std::mutex mu;
+    static cudaStream_t streams[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev]) {
+        e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    out = streams[dev];
+    return cudaSuccess;
+}
+
 // The column-split kernels (which can store p inside the mode-S pass) take
 // these shapes.
 static bool split_shape(int vec_ok, int64_t n, int h, const int *start) {
@@ -131,9 +149,50 @@ static cudaError_t dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float
 #if HH_SPLIT8
         // larger h: clusters of eight CTAs, each keeping 512 columns of every
         // reflector (32 threads x 16 columns x 8 rows per row group)
-        if (n > 2048 && n <= 4096 && !start && h <= split::max_h<32, 4, 8, 8, 4>())
+        if (n > 2048 && n <= 4096 && !start && h <= split::max_h<32, 4, 8, 8, 4>()) {
+            int ncl = 0;
+            cudaError_t e = split::resident_clusters<32, 4, 8, 8, 4, 8, 1>(mode, ncl);
+            if (e != cudaSuccess) return e;
+            // Eight-CTA clusters cannot fill every SM (a GPC's SMs are not a
+            // multiple of eight).  The SMs they leave run the staged kernel on
+            // a share of the rows, on a second stream ordered by events; per
+            // SM the cluster kernel is about 1.3x as fast.  The cluster launch
+            // takes the highest priority so that its CTAs are placed first.
+            // (Requests that keep p stay on the cluster kernel.)
+            constexpr int64_t kUnit = 64;  // rows of one cluster round: 8 groups x 8 rows
+            const int idle = num_sms - 8 * ncl;
+            if (!P && idle > 0 && batch >= (int64_t)num_sms * kUnit) {
+                const double w8 = 1.3 * 8.0 * ncl, ws = (double)idle;
+                const int64_t b1 = (int64_t)((double)batch * w8 / (w8 + ws)) / kUnit * kUnit;
+                cudaStream_t side = nullptr;
+                if ((e = side_stream(side)) != cudaSuccess) return e;
+                cudaEvent_t fork = nullptr, join = nullptr;
+                if ((e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess)
+                    return e;
+                if ((e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) != cudaSuccess) {
+                    cudaEventDestroy(fork);
+                    return e;
+                }
+                e = cudaEventRecord(fork, st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+                if (e == cudaSuccess)
+                    e = split::launch<32, 4, 8, 8, 4, 8, 1>(mode, X, ldx, Y, ldy, b1, ni, U, tau,
+                                                            ldv, h, gram, sign, d, err, st,
+                                                            nullptr, 0, true);
+                if (e == cudaSuccess)
+                    e = staged::launch<HH_N4096_G, HH_N4096_NG, HH_N4096_RT, HH_N4096_RG,
+                                       HH_N4096_B>(mode, X + b1 * ldx, ldx, Y + b1 * ldy, ldy,
+                                                   batch - b1, ni, U, tau, ldv, h, gram, sign, d,
+                                                   err, idle, side, nullptr);
+                if (e == cudaSuccess) e = cudaEventRecord(join, side);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
+                cudaEventDestroy(fork);
+                cudaEventDestroy(join);
+                return e;
+            }
             return split::launch<32, 4, 8, 8, 4, 8, 1>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv,
                                                        h, gram, sign, d, err, st, P, ldp);
+        }
 #endif
 #endif
         if (n <= 4096) return HH_STAGED(HH_N4096_G, HH_N4096_NG, HH_N4096_RT, HH_N4096_RG, HH_N4096_B);

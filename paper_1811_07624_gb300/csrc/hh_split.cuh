@@ -436,48 +436,91 @@ constexpr int max_h() {
     return (int)(max_smem<MINB>() / (XCfg<G, NG, RT, RG, B>::HALF * sizeof(float)));
 }
 
-// CL CTAs per cluster split the columns (CTA r owns [r*HALF, (r+1)*HALF));
-// MINB CTAs per SM bound the registers.  Mode S with P also writes
-// p = W^T (sigma .* x) (rows of P, leading dimension ldp, 16-byte aligned).
-template <int G, int NG, int RT, int RG, int B, int CL = 2, int MINB = 1>
-cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
-                   int64_t batch, int n, const float *V, const float *tau, int64_t ldv, int h,
-                   const float *gram, const float *sign, const float *d, int *err,
-                   cudaStream_t st, float *P = nullptr, int64_t ldp = 0) {
+// Per configuration, kernel (W, W^T, S, S keeping p) and device: the
+// shared-memory opt-in at the largest request and the co-resident clusters
+// measured with it.
+template <int G, int NG, int RT, int RG, int B, int CL, int MINB>
+inline PerDevice g_state[4];
+
+template <int G, int NG, int RT, int RG, int B, int CL, int MINB, typename K>
+cudaError_t cluster_occupancy(K kern, int si, int &ncl) {
     using C = XCfg<G, NG, RT, RG, B>;
     constexpr size_t kMaxSmem = max_smem<MINB>();
-    if (n < 1 || n > CL * C::HALF || n % 4 || ldv < CL * C::HALF || ldv % 4 ||
-        h > max_h<G, NG, RT, RG, B, MINB>())
-        return cudaErrorInvalidValue;
-    const size_t smem = h > 0 ? (size_t)h * C::HALF * sizeof(float) : 16;
-    // per kernel (one per mode) and device: the shared-memory opt-in at the
-    // largest request, and the co-resident clusters measured with it
-    static PerDevice state[4];  // W, W^T, S, S keeping p
-    auto run = [&](auto kern, int si) -> cudaError_t {
-        cudaLaunchConfig_t cfg = {};
+    return per_device(g_state<G, NG, RT, RG, B, CL, MINB>[si], ncl, [&](int &v) -> cudaError_t {
+        cudaError_t e2 =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (e2 != cudaSuccess) return e2;
+        cudaLaunchConfig_t q = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = CL;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
+        q.blockDim = dim3(C::THREADS);
+        q.gridDim = dim3(CL);
+        q.dynamicSmemBytes = kMaxSmem;
+        q.attrs = attr;
+        q.numAttrs = 1;
+        int nc = 0;
+        e2 = cudaOccupancyMaxActiveClusters(&nc, kern, &q);
+        if (e2 != cudaSuccess) return e2;
+        v = nc > 0 ? nc : 1;
+        return cudaSuccess;
+    });
+}
+
+// Clusters of the mode's kernel (without p) that can be resident at once.
+template <int G, int NG, int RT, int RG, int B, int CL = 2, int MINB = 1>
+cudaError_t resident_clusters(hh_mode mode, int &ncl) {
+    switch (mode) {
+        case HH_MODE_W:
+            return cluster_occupancy<G, NG, RT, RG, B, CL, MINB>(
+                split_chain_kernel<HH_MODE_W, G, NG, RT, RG, B, CL, MINB>, 0, ncl);
+        case HH_MODE_WT:
+            return cluster_occupancy<G, NG, RT, RG, B, CL, MINB>(
+                split_chain_kernel<HH_MODE_WT, G, NG, RT, RG, B, CL, MINB>, 1, ncl);
+        default:
+            return cluster_occupancy<G, NG, RT, RG, B, CL, MINB>(
+                split_chain_kernel<HH_MODE_SYM, G, NG, RT, RG, B, CL, MINB>, 2, ncl);
+    }
+}
+
+// CL CTAs per cluster split the columns (CTA r owns [r*HALF, (r+1)*HALF));
+// MINB CTAs per SM bound the registers.  Mode S with P also writes
+// p = W^T (sigma .* x) (rows of P, leading dimension ldp, 16-byte aligned).
+// high_priority: the launch takes the device's highest scheduling priority
+// (for a launch that shares the GPU with one on another stream).
+template <int G, int NG, int RT, int RG, int B, int CL = 2, int MINB = 1>
+cudaError_t launch(hh_mode mode, const float *X, int64_t ldx, float *Y, int64_t ldy,
+                   int64_t batch, int n, const float *V, const float *tau, int64_t ldv, int h,
+                   const float *gram, const float *sign, const float *d, int *err,
+                   cudaStream_t st, float *P = nullptr, int64_t ldp = 0,
+                   bool high_priority = false) {
+    using C = XCfg<G, NG, RT, RG, B>;
+    if (n < 1 || n > CL * C::HALF || n % 4 || ldv < CL * C::HALF || ldv % 4 ||
+        h > max_h<G, NG, RT, RG, B, MINB>())
+        return cudaErrorInvalidValue;
+    const size_t smem = h > 0 ? (size_t)h * C::HALF * sizeof(float) : 16;
+    int prio_least = 0, prio_greatest = 0;
+    if (high_priority) {
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+        if (e != cudaSuccess) return e;
+    }
+    auto run = [&](auto kern, int si) -> cudaError_t {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributePriority;
+        attr[1].val.priority = prio_greatest;
         cfg.blockDim = dim3(C::THREADS);
         cfg.stream = st;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = high_priority ? 2 : 1;
         int ncl = 1;
-        cudaError_t e = per_device(state[si], ncl, [&](int &v) -> cudaError_t {
-            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)kMaxSmem);
-            if (e2 != cudaSuccess) return e2;
-            cudaLaunchConfig_t q = cfg;
-            q.gridDim = dim3(CL);
-            q.dynamicSmemBytes = kMaxSmem;
-            int nc = 0;
-            e2 = cudaOccupancyMaxActiveClusters(&nc, kern, &q);
-            if (e2 != cudaSuccess) return e2;
-            v = nc > 0 ? nc : 1;
-            return cudaSuccess;
-        });
+        cudaError_t e = cluster_occupancy<G, NG, RT, RG, B, CL, MINB>(kern, si, ncl);
         if (e != cudaSuccess) return e;
         const int64_t groups = ((batch + RT - 1) / RT + RG - 1) / RG;  // row-group tiles / RG
         const int grid_cl = (int)(groups < ncl ? groups : ncl);

@@ -116,6 +116,36 @@ def test_f32_eight_cta_clusters(n, h):
         _check(mode, n, h, 21, torch.float32, seed=n + h)
 
 
+@pytest.mark.parametrize("inplace", [False, True])
+def test_f32_eight_cta_clusters_with_idle_sm_fill(inplace):
+    # A batch large enough that the SMs eight-CTA clusters leave idle run the
+    # staged kernel on a share of the rows beside them: every row is written
+    # (no NaN left) and the rows sampled everywhere, densely around the
+    # possible split points, match the oracle.
+    n, h, B = 4096, 40, 12000
+    U = si.reflectors(n, h, seed=11, unit=False)
+    d = si.spectrum(n, seed=11)
+    s = si.sign(n, seed=11)
+    plan = _plan(U, d=d, sign=s, dtype=torch.float32)
+    X = torch.as_tensor(si.vectors(B, n, seed=11), dtype=torch.float32, device=DEV)
+    idx = np.unique(np.concatenate([np.linspace(0, B - 1, 97).astype(np.int64),
+                                    np.arange(8960, 10560, 8), np.arange(B - 70, B)]))
+    Xs = _as64(X[torch.as_tensor(idx, device=DEV)])
+    for mode in ("W", "WT", "SYM"):
+        if inplace:
+            Xg = X.clone()
+            Y = plan.apply_mode(mode, Xg, out=Xg)
+        else:
+            Y = plan.apply_mode(mode, X, out=torch.full((B, n), float("nan"), device=DEV))
+        plan.sync()
+        assert bool(torch.isfinite(Y).all()), f"{mode}: unwritten rows"
+        ref = oracle.apply(mode, _as64(torch.as_tensor(U, dtype=torch.float32)), Xs, sign=s,
+                           d=_as64(torch.as_tensor(d, dtype=torch.float32)))
+        got = _as64(Y[torch.as_tensor(idx, device=DEV)])
+        assert _rel(got, ref) <= TOL[torch.float32], f"{mode}: rel err {_rel(got, ref):.3e}"
+    plan.close()
+
+
 @pytest.mark.parametrize("batch", [0, 1, 2, 7, 8, 9, 31, 33, 513])
 def test_batch_tails(batch):
     for n in (256, 1000, 4096):
