@@ -114,7 +114,7 @@ def row_kind(name):
 
 
 def profiled_traffic(row, units, path=None):
-    """DRAM bytes (read + write) of one launch of `row` over `units` vectors, from
+    """DRAM bytes (read + write) of one call of `row` over `units` vectors, from
     the ncu figures recorded in profiles/traffic.json, scaled by units; None
     when there is no figure or the row's kernel sources changed since."""
     path = path or TRAFFIC_JSON
@@ -154,18 +154,27 @@ def ncu_dram_bytes(csv_path):
     return [(got[i]["dram__bytes_read.sum"], got[i]["dram__bytes_write.sum"]) for i in order]
 
 
-def ingest_traffic(csv_path, rows, out_path, command):
-    """Record the DRAM bytes of the launches captured in an ncu log: launch i is
-    the first launch of rows[i] (each at its full batch)."""
+def ingest_traffic(csv_path, rows, out_path, command, per_row=None):
+    """Record the DRAM bytes of the launches captured in an ncu log: the log
+    holds the first call of each of rows (at its full batch) in order, per_row[i]
+    consecutive launches for rows[i] (default 1), summed."""
     entries = []
     if os.path.exists(out_path):
         with open(out_path) as f:
             entries = json.load(f).get("entries", [])
+    per_row = per_row or [1] * len(rows)
+    if len(per_row) != len(rows):
+        raise ValueError("one launch count per row")
     launches = ncu_dram_bytes(csv_path)
-    if len(launches) < len(rows):
-        raise ValueError(f"{csv_path}: {len(launches)} launches for {len(rows)} rows")
+    if len(launches) < sum(per_row):
+        raise ValueError(f"{csv_path}: {len(launches)} launches for {sum(per_row)}")
     full = step_vectors(rows)
-    for row, (rd, wr) in zip(rows, launches):
+    summed, k = [], 0
+    for c in per_row:
+        part = launches[k:k + c]
+        summed.append((sum(p[0] for p in part), sum(p[1] for p in part)))
+        k += c
+    for row, (rd, wr) in zip(rows, summed):
         entries = [e for e in entries if e.get("row") != row]
         entries.append({"row": row, "units": full[row], "dram_read_bytes": rd,
                         "dram_write_bytes": wr, "sources": ROW_SOURCES[row_kind(row)],
@@ -173,10 +182,10 @@ def ingest_traffic(csv_path, rows, out_path, command):
                         "command": command})
     entries.sort(key=lambda e: e["row"])
     with open(out_path, "w") as f:
-        json.dump({"about": "DRAM bytes of one launch per row (ncu dram__bytes_read.sum and "
-                            "dram__bytes_write.sum, one pass, --clock-control none), at the "
-                            "row's full batch; bench.py uses a figure only while the row's "
-                            "kernel sources hash to sources_sha256",
+        json.dump({"about": "DRAM bytes of one call per row, summed over its launches (ncu "
+                            "dram__bytes_read.sum and dram__bytes_write.sum, one pass, "
+                            "--clock-control none), at the row's full batch; bench.py uses a "
+                            "figure only while the row's kernel sources hash to sources_sha256",
                    "entries": entries}, f, indent=1)
         f.write("\n")
 
@@ -280,7 +289,10 @@ class ChainRow:
         # its own first call)
         self.Y = _SHARED[("Y",) + key]
         self.torch = torch
-        self.launches = 1
+        # 2048 < n <= 4096 with 25 < h <= 100 at a large batch: the eight-CTA cluster
+        # kernel and, on the SMs its clusters leave, the staged kernel beside it
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        self.launches = 2 if (2048 < n <= 4096 and 25 < h <= 100 and batch >= sms * 64) else 1
         self.bound = "hbm" if (self.flops() / self.bytes()) < 11.9 else "alu"
         _CHAIN_ROWS.append(self)
 
@@ -1036,11 +1048,14 @@ def main():
     ap.add_argument("--traffic-out", default=TRAFFIC_JSON)
     ap.add_argument("--traffic-command", default="",
                     help="the ncu command line that wrote the log")
+    ap.add_argument("--traffic-launches", default="",
+                    help="launches per row in the log, comma separated (default 1 each)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     names = [r for r in args.rows.split(",") if r]
     if args.ingest_traffic:
-        ingest_traffic(args.ingest_traffic, names, args.traffic_out, args.traffic_command)
+        per = [int(c) for c in args.traffic_launches.split(",") if c] or None
+        ingest_traffic(args.ingest_traffic, names, args.traffic_out, args.traffic_command, per)
         return 0
     global TUNE_TABLE
     TUNE_TABLE = args.tune_table

@@ -31,8 +31,11 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+# shapes where the unskipped apply runs the staged kernel too (the column-split
+# kernels take h <= 50 at n <= 1024 and h <= 100 at 2048 < n <= 4096), so that
+# skipping the exact zeros must give bit-identical results
 @pytest.mark.parametrize("n,h,B", [(1024, 256, 1000), (1000, 96, 777), (2048, 128, 513),
-                                   (4096, 64, 130)])
+                                   (4096, 128, 130)])
 def test_partial_qr_reflectors_skip_and_match(dev, n, h, B):
     import oracle
     from paper_1811_07624_gb300 import Plan
