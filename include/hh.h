@@ -32,6 +32,11 @@
  *    stream).  Apply, backward and distance calls are asynchronous on it:
  *    argument errors are reported synchronously, kernel results are ready
  *    when the stream is.  hh_create and hh_destroy synchronise `stream`.
+ *    An F32 apply with 2048 < n <= 4096 and 25 < h <= 100 on a large batch
+ *    runs part of its rows on a second stream of the library's, forked from
+ *    and joined back to `stream` by events; that stream and its events are
+ *    created by the first such call on a device, which should run outside
+ *    stream capture.
  *  - In-place (Y == X, same ld) is allowed for the three apply calls.
  *    Other overlaps between inputs and outputs are undefined.
  *  - A plan is read-only after hh_create, so one plan may be used from

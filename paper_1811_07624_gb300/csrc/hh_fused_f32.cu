@@ -48,21 +48,30 @@
 
 namespace hh {
 
-// A second stream per device (non-blocking, created on first use), on which
-// a launch can run part of its work beside the caller's stream.
-static cudaError_t side_stream(cudaStream_t &out) {
-    static std::mutex mu;
-    static cudaStream_t streams[kMaxDevices] = {};
+// A second stream per device (non-blocking) with a fork and a join event,
+// created on first use (so that a call inside stream capture creates
+// nothing): a launch runs part of its work on it beside the caller's stream.
+// The mutex also keeps one call's event records and waits together.
+struct Side {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+static std::mutex g_side_mu;
+
+static cudaError_t side_for_device(Side *&out) {
+    static Side sides[kMaxDevices];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!streams[dev]) {
-        e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
-        if (e != cudaSuccess) return e;
+    Side &sd = sides[dev];
+    if (!sd.stream) {
+        if ((e = cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&sd.stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
     }
-    out = streams[dev];
+    out = &sd;
     return cudaSuccess;
 }
 
@@ -164,17 +173,12 @@ static cudaError_t dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float
             if (!P && idle > 0 && batch >= (int64_t)num_sms * kUnit) {
                 const double w8 = 1.3 * 8.0 * ncl, ws = (double)idle;
                 const int64_t b1 = (int64_t)((double)batch * w8 / (w8 + ws)) / kUnit * kUnit;
-                cudaStream_t side = nullptr;
-                if ((e = side_stream(side)) != cudaSuccess) return e;
-                cudaEvent_t fork = nullptr, join = nullptr;
-                if ((e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess)
-                    return e;
-                if ((e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) != cudaSuccess) {
-                    cudaEventDestroy(fork);
-                    return e;
-                }
-                e = cudaEventRecord(fork, st);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+                std::lock_guard<std::mutex> lock(g_side_mu);
+                Side *sd = nullptr;
+                if ((e = side_for_device(sd)) != cudaSuccess) return e;
+                cudaStream_t side = sd->stream;
+                e = cudaEventRecord(sd->fork, st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(side, sd->fork, 0);
                 if (e == cudaSuccess)
                     e = split::launch<32, 4, 8, 8, 4, 8, 1>(mode, X, ldx, Y, ldy, b1, ni, U, tau,
                                                             ldv, h, gram, sign, d, err, st,
@@ -184,10 +188,8 @@ static cudaError_t dispatch_f32(hh_mode mode, const float *X, int64_t ldx, float
                                        HH_N4096_B>(mode, X + b1 * ldx, ldx, Y + b1 * ldy, ldy,
                                                    batch - b1, ni, U, tau, ldv, h, gram, sign, d,
                                                    err, idle, side, nullptr);
-                if (e == cudaSuccess) e = cudaEventRecord(join, side);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
-                cudaEventDestroy(fork);
-                cudaEventDestroy(join);
+                if (e == cudaSuccess) e = cudaEventRecord(sd->join, side);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, sd->join, 0);
                 return e;
             }
             return split::launch<32, 4, 8, 8, 4, 8, 1>(mode, X, ldx, Y, ldy, batch, ni, U, tau, ldv,

@@ -146,6 +146,32 @@ def test_f32_eight_cta_clusters_with_idle_sm_fill(inplace):
     plan.close()
 
 
+def test_idle_sm_fill_in_cuda_graph():
+    # the cluster kernel and the staged kernel on the idle SMs fork to a second
+    # stream and join back: the pair captures into a CUDA graph and replays to
+    # the eager result
+    n, h, B = 4096, 40, 12000
+    U = si.reflectors(n, h, seed=21, unit=False)
+    plan = _plan(U, dtype=torch.float32)
+    X = torch.as_tensor(si.vectors(B, n, seed=21), dtype=torch.float32, device=DEV)
+    Y_eager = plan.apply(X)  # the first call creates the second stream, outside capture
+    Yg = torch.empty_like(X)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.apply(X, out=Yg)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.apply(X, out=Yg)
+    Yg.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    plan.sync()
+    assert torch.equal(Yg, Y_eager)
+    plan.close()
+
+
 @pytest.mark.parametrize("batch", [0, 1, 2, 7, 8, 9, 31, 33, 513])
 def test_batch_tails(batch):
     for n in (256, 1000, 4096):
