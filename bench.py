@@ -81,7 +81,8 @@ ROW_SOURCES = {
     "mahalanobis": [_CSRC + "hh_mahalanobis.cu", _CSRC + "hh_fused.cuh"],
     "mahalanobis_grad": [_CSRC + "hh_backward.cu", _CSRC + "hh_fused.cuh"] + _CHAIN_SRC,
     "adjoint": [_CSRC + "hh_backward.cu", _CSRC + "hh_fused.cuh"] + _CHAIN_SRC,
-    "batched": [_CSRC + "hh_batched.cu", _CSRC + "hh_staged.cuh", _CSRC + "hh_fused.cuh"],
+    "batched": [_CSRC + "hh_batched.cu", _CSRC + "hh_staged.cuh", _CSRC + "hh_fused.cuh",
+                _CSRC + "hh_split.cuh"],
     "trunc": _CHAIN_SRC,
 }
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
@@ -719,14 +720,27 @@ class BatchedRow:
             self.Xs.append(self.Xbuf[off:off + n * b].view(b, n))
             self.Ys.append(self.Ybuf[off:off + n * b].view(b, n))
             off += n * b
-        self.launches = 1
         self.bound = "hbm" if self.flops() / self.bytes() < 11.9 else "alu"
         info = self.batch.info()
         shapes = hh.batch_shapes()
+        # kernels in the graph: one per cluster size of the resident shape in use,
+        # and one for the staged shapes
+        kinds = set()
+        for (n, _, b, _), k in zip(self.specs, info["shapes"]):
+            if b > 0:
+                cl = shapes[k]["max_cluster"]
+                kinds.add(-(-n // (shapes[k]["cover"] // cl)) if cl else 0)
+        self.launches = len(kinds)
+
+        def label(k):
+            s = shapes[k]
+            base = f"{k}:G{s['G']}xNG{s['NG']}xRT{s['RT']}"
+            return base + (f" resident, <= {s['max_cluster']} CTAs" if s["max_cluster"] else "")
+
         self.info = {"items": info["items"], "grid": info["grid"], "tune_s": self.tune_s,
-                     "tune": self.tune_source,
-                     "shape_use": {f"{k}:G{shapes[k]['G']}xNG{shapes[k]['NG']}xRT{shapes[k]['RT']}":
-                                   info["shapes"].count(k) for k in sorted(set(info["shapes"]))}}
+                     "tune": self.tune_source, "launches": self.launches,
+                     "shape_use": {label(k): info["shapes"].count(k)
+                                   for k in sorted(set(info["shapes"]))}}
 
     def vectors(self):
         return sum(b for _, _, b, _ in self.specs)

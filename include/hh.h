@@ -292,8 +292,9 @@ hh_status hh_batch_create(hh_batch_t *out, int count, const hh_plan_t *plans,
  * arrays of count device pointers (16-byte aligned, rows of n floats);
  * ldx, ldy: host arrays of count row strides (multiples of 4, >= n), or NULL
  * for n.  X[i] == Y[i] is allowed with equal strides.  The first call per mode
- * captures the launch (a counter reset and the kernel) in a CUDA graph; every
- * call replays it on `stream`.  When the pointers or strides differ from the
+ * captures the launches (one per cluster size of the resident shape, then a
+ * counter reset and the staged-shape kernel, each only where it has work) in
+ * a CUDA graph; every call replays it on `stream`.  When the pointers or strides differ from the
  * previous call, the task table is first copied to the device on `stream`.
  * Stream-ordered; calls on different streams must not overlap on the GPU
  * (they share the work counter).
@@ -314,9 +315,24 @@ hh_status hh_batch_destroy(hh_batch_t batch);
 
 /* Tile shapes of the batched kernel, 0 .. hh_batch_num_shapes()-1: G threads
  * per row group, NG granules of 4 floats and RT rows per thread, rows per tile,
- * and the largest n the shape covers (G * NG * 4). */
+ * and the largest n the shape covers (G * NG * 4 for a staged shape).
+ *
+ * Staged shapes stream every tile's rows through shared memory and read the
+ * reflectors from L2 once per tile, with work items taken from a shared
+ * counter.  The resident shape (hh_batch_shape_limits reports max_cluster > 0)
+ * splits each vector's columns over a cluster of ceil(n / (G * NG * 4)) CTAs,
+ * up to max_cluster, keeps each CTA's columns of all h <= max_h reflectors of
+ * one transform in shared memory, and runs a static, transform-ordered
+ * schedule built at hh_batch_create: one launch per cluster size, each
+ * cluster loading a transform's reflectors once.  The launches of one batch
+ * and mode are captured in the same graph.  Any output pointer of either
+ * kind of shape is a plain pointer argument (NULL skips it). */
 int hh_batch_num_shapes(void);
 hh_status hh_batch_shape(int shape, int *G, int *NG, int *RT, int *rows_per_tile, int *cover);
+/* max_h: the largest h the shape takes (-1: no limit); max_cluster: CTAs per
+ * cluster of the resident shape (0 for a staged shape).  HH_ERR_INVALID_ARG
+ * for a shape outside [0, hh_batch_num_shapes()). */
+hh_status hh_batch_shape_limits(int shape, int *max_h, int *max_cluster);
 
 /*
  * Autotuner.  hh_tune times, for every (n, h) in ns x hs, each tile shape that
@@ -327,7 +343,7 @@ hh_status hh_batch_shape(int shape, int *G, int *NG, int *RT, int *rows_per_tile
  * use for (n, h): the table entry, else the entry of the nearest h for the same
  * n, else a fixed rule; and the measured milliseconds per shape (hh_batch_num_
  * shapes() floats, NaN where not measured), or NULL.  hh_tune_set pins an
- * entry.  hh_tune_save / hh_tune_load write / merge the table as text lines
+ * entry (HH_ERR_INVALID_ARG where the shape does not take (n, h)).  hh_tune_save / hh_tune_load write / merge the table as text lines
  * "n h shape".  hh_tune_clear empties it.  Host-only except hh_tune.
  */
 hh_status hh_tune(const int64_t *ns, int nn, const int64_t *hs, int nh, int64_t rows,

@@ -72,6 +72,7 @@ SIGNATURES = {
     "hh_batch_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(ip), ctypes.POINTER(ip)],
     "hh_batch_destroy": [vp],
     "hh_batch_shape": [ip] + [ctypes.POINTER(ip)] * 5,
+    "hh_batch_shape_limits": [ip] + [ctypes.POINTER(ip)] * 2,
     "hh_tune": [ctypes.POINTER(i64), ip, ctypes.POINTER(i64), ip, i64, vp],
     "hh_tune_get": [i64, i64, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_float)],
     "hh_tune_set": [i64, i64, ip],

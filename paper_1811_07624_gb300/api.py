@@ -348,12 +348,18 @@ class Batch:
 
 
 def batch_shapes() -> list[dict]:
-    """The tile shapes compiled into the batched kernel."""
+    """The tile shapes compiled into the batched kernel: G, NG, RT, rows_per_tile,
+    cover, max_h (-1: no limit) and max_cluster (CTAs per cluster of the
+    resident-reflector shape; 0 for a staged shape)."""
     out = []
     for s in range(_lib.lib().hh_batch_num_shapes()):
         v = [ctypes.c_int() for _ in range(5)]
         _lib.call("hh_batch_shape", s, *[ctypes.byref(x) for x in v])
-        out.append(dict(zip(("G", "NG", "RT", "rows_per_tile", "cover"), [x.value for x in v])))
+        d = dict(zip(("G", "NG", "RT", "rows_per_tile", "cover"), [x.value for x in v]))
+        mh, mc = ctypes.c_int(), ctypes.c_int()
+        _lib.call("hh_batch_shape_limits", s, ctypes.byref(mh), ctypes.byref(mc))
+        d.update(max_h=mh.value, max_cluster=mc.value)
+        out.append(d)
     return out
 
 

@@ -24,6 +24,14 @@
 // untuned shapes fall back to the nearest tuned h for that n, then to a fixed
 // rule.
 //
+// Resident shape.  A further shape keeps each transform's reflectors in shared
+// memory instead of reading them from L2 once per tile: clusters of
+// ceil(n / 512) CTAs split the columns as the single-transform column-split
+// kernel does, one launch per cluster size, each on a static schedule that
+// hands every cluster a contiguous stretch of its tasks (see
+// cluster_batch_kernel).  The autotuner times it beside the staged shapes.
+// All launches of a batch and mode are captured in one graph.
+//
 // Streams.  A batch's work counter and task table are shared by its launches;
 // a launch on a stream other than the previous launch's first waits for that
 // launch (an event), so calls on different streams never overlap on them.
@@ -36,13 +44,18 @@
 #include <utility>
 #include <vector>
 
-#include "hh_staged.cuh"
+#include "hh_split.cuh"
 
 namespace hh {
 namespace batched {
 
+#ifndef HH_BATCH_FORK
+#define HH_BATCH_FORK 1  // the launches of one graph on parallel branches (0: in sequence)
+#endif
+
 constexpr int kThreads = 256;
-constexpr int kNumShapes = 10;
+constexpr int kNumShapes = 11;
+constexpr int kClusterShape = 10;        // resident reflectors, clusters of CTAs (below)
 constexpr int kStageBytes = 128 * 1024;  // >= ROWS * COVER * 4 for every shape
 constexpr int kRedFloats = 512;          // >= 2 * RG * (B * RT) * NW for every shape
 
@@ -60,8 +73,15 @@ static const ShapeInfo kShape[kNumShapes] = {
     {128, 4, 4, 4},   // 7: COVER 2048,   8 rows,  64 floats, 4 reflectors per round
     {128, 8, 4, 2},   // 8: COVER 4096,   8 rows, 128 floats
     {32, 4, 8, 4},    // 9: COVER  512,  64 rows, 128 floats, 4 reflectors per round
+    {32, 4, 8, 4},    // 10: resident reflectors, 512 columns per CTA, clusters of up to
+                      //     four CTAs: COVER 2048, 64 rows, h <= 100
 };
-inline int shape_cover(int s) { return kShape[s].G * kShape[s].NG * 4; }
+constexpr int kClusterHalf = 512;    // columns of one CTA of the resident shape
+constexpr int kClusterMaxCL = 4;     // CTAs per cluster: n <= 4 * 512
+constexpr int kClusterMaxH = 100;    // h * 512 floats <= 200 KiB of shared memory
+inline int shape_cover(int s) {
+    return s == kClusterShape ? kClusterMaxCL * kClusterHalf : kShape[s].G * kShape[s].NG * 4;
+}
 inline int shape_rows(int s) { return kShape[s].RT * (kThreads / kShape[s].G); }
 constexpr int kMaxN = 4096;
 
@@ -259,6 +279,197 @@ batched_chain_kernel(const Task *__restrict__ tasks, const Item *__restrict__ it
     }
 }
 
+// ---- resident-reflector tiles (shape kClusterShape) ----
+//
+// The transforms of this shape run on the column-split kernel's layout
+// (split::chain): a cluster of CL = ceil(n / 512) CTAs splits every vector's
+// columns, 512 per CTA, and each CTA holds its columns of all h reflectors in
+// shared memory while it works on that transform, so no reflector value is
+// read from L2 inside the row loop.  One kernel per CL (1..4) takes a static,
+// transform-ordered schedule built on the host: cluster c walks items
+// cstart[c] .. cstart[c+1]-1, each a run of rows of one task, and loads a
+// task's reflectors once, when its first item begins.  Row group rg of every
+// CTA of the cluster takes the same tiles of RT rows of an item
+// (rg, rg + RG, ...), so the per-round exchange of partial dot products pairs
+// up across the cluster exactly as in the single-transform kernel.
+constexpr int kCG = 32, kCNG = 4, kCRT = 8, kCRG = kThreads / kCG, kCB = 4;
+using CCfg = split::XCfg<kCG, kCNG, kCRT, kCRG, kCB>;
+static_assert(CCfg::HALF == kClusterHalf, "resident shape: 512 columns per CTA");
+static_assert(CCfg::THREADS == kThreads, "resident shape: 256 threads");
+constexpr int kClusterUnit = kCRT * kCRG;  // rows of one pass of the row groups
+constexpr int kClusterSmem = kClusterMaxH * kClusterHalf * 4;
+
+// Rows [r0, r1) of task `task`.
+struct CItem {
+    int task, pad;
+    int64_t r0, r1;
+};
+
+// Scale the first `act` granules of the held columns (this CTA's, from s) by s.
+__device__ __forceinline__ void cscale(float2 (&x)[kCRT][CCfg::E2], const float *__restrict__ s,
+                                       int t, int act, int ncols) {
+#pragma unroll
+    for (int i = 0; i < kCNG; ++i) {
+        if (i >= act) break;
+        const int col = (t + kCG * i) * 4;
+        if (col >= ncols) continue;
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(s + col));
+        const float2 lo = make_float2(q.x, q.y), hi = make_float2(q.z, q.w);
+#pragma unroll
+        for (int r = 0; r < kCRT; ++r) {
+            x[r][2 * i] = __fmul2_rn(x[r][2 * i], lo);
+            x[r][2 * i + 1] = __fmul2_rn(x[r][2 * i + 1], hi);
+        }
+    }
+}
+
+// Requirements (checked on the host): every task of the launch has
+// (CL - 1) * 512 < n <= CL * 512, n % 4 == 0, h <= kClusterMaxH, V rows zero
+// padded to at least round_up(n, 128) columns, X and Y 16-byte aligned with
+// ldx % 4 == 0 and ldy % 4 == 0; items of a cluster in task order; the
+// dynamic shared memory holds max h * 512 floats.  Waits are bounded: on
+// expiry the status word gets HH_ERR_TIMEOUT, no further reflector copy is
+// issued, and the copy in flight gets one more bounded wait before the CTA
+// leaves.
+template <int MODE, int CL>
+__global__ void __launch_bounds__(kThreads, 1)
+cluster_batch_kernel(const Task *__restrict__ tasks, const CItem *__restrict__ items,
+                     const int *__restrict__ cstart, int *__restrict__ err) {
+    constexpr int G = kCG, NG = kCNG, RT = kCRT, RG = kCRG, B = kCB;
+    constexpr int E2 = CCfg::E2, NV = CCfg::NV, NW = CCfg::NW, HALF = CCfg::HALF;
+    float *vs = b_stage;  // h x HALF: this CTA's columns of the current task's reflectors
+    __shared__ __align__(8) uint64_t vbar;
+    __shared__ __align__(8) uint64_t rbar[RG][2];
+    __shared__ __align__(16) float rslot[RG][2 * CL * NW * NV];
+    __shared__ int aborted;
+
+    const int tid = threadIdx.x;
+    const int rg = tid / G;
+    const int t = tid - rg * G;
+    const int warp = t >> 5, lane = t & 31;
+    const uint32_t rank = split::cluster_rank();
+    const int c0 = (int)rank * HALF;
+    const int cid = (int)split::cluster_id();
+
+    if (tid == 0) {
+        aborted = 0;
+        staged::mbar_init(&vbar, 1);
+        for (int g = 0; g < RG; ++g) {
+            staged::mbar_init(&rbar[g][0], NW);
+            staged::mbar_init(&rbar[g][1], NW);
+        }
+        split::fence_mbarrier_init();
+        staged::fence_proxy_async();
+    }
+    // every mbarrier of the cluster is initialised before any peer stores into it
+    split::cluster_sync();
+    split::Exchange<CL> xc;
+    xc.round = 0;
+    xc.rank = rank;
+#pragma unroll
+    for (int pc = 0; pc < CL - 1; ++pc) {
+        const uint32_t other = (rank + 1u + (uint32_t)pc) % (uint32_t)CL;
+        xc.peer_slot[pc] = split::peer_addr(staged::smem_u32(&rslot[rg][0]), other);
+        xc.peer_bar[pc] = split::peer_addr(staged::smem_u32(&rbar[rg][0]), other);
+    }
+    xc.waiting = true;
+
+    uint32_t vphase = 0, last_par = 0;
+    int issued = 0, confirmed = 0;  // reflector copies of thread 0, and those seen complete
+    int cur = -1;
+    const int i1 = cstart[cid + 1];
+    for (int it = cstart[cid]; it < i1; ++it) {
+        const CItem item = items[it];
+        const Task &tk = tasks[item.task];
+        const int n = tk.n, h = tk.h;
+        const int ncols = n - c0 < HALF ? n - c0 : HALF;  // >= 1 for CL = ceil(n / HALF)
+        const int act = (ncols + G * 4 - 1) / (G * 4);   // granules of a thread inside n
+        if (item.task != cur) {
+            __syncthreads();  // every row group is done with the previous reflectors
+            if (h > 0) {
+                if (tid == 0 && !*(volatile int *)&aborted) {
+                    staged::fence_proxy_async();
+                    const uint32_t rowb = (uint32_t)act * G * 16u;
+                    staged::mbar_expect_tx(&vbar, rowb * (uint32_t)h);
+                    for (int k = 0; k < h; ++k)
+                        staged::bulk_g2s(vs + (size_t)k * HALF, tk.V + (size_t)k * tk.ldv + c0, rowb,
+                                         &vbar);
+                    ++issued;
+                    last_par = vphase;
+                }
+                if (!*(volatile int *)&aborted) {
+                    if (split::wait_cluster_bounded(&vbar, vphase)) {
+                        if (tid == 0) ++confirmed;
+                    } else {
+                        atomicExch(err, (int)HH_ERR_TIMEOUT);
+                        *(volatile int *)&aborted = 1;
+                    }
+                }
+                vphase ^= 1u;
+            }
+            cur = item.task;
+        }
+        const float *X = tk.X;
+        float *Y = tk.Y;
+        const int64_t ldx = tk.ldx, ldy = tk.ldy, rb = item.r0, re = item.r1;
+        const int64_t ntl = (re - rb + RT - 1) / RT;
+        for (int64_t tl = rg; tl < ntl; tl += RG) {
+            const int64_t r0 = rb + tl * RT;
+            // the group's next tile of this item into L2 while this one is computed
+            if (t == 0) {
+                const int64_t nr0 = r0 + (int64_t)RG * RT;
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+                    if (nr0 + r < re) split::prefetch_l2(X + (nr0 + r) * ldx + c0, (uint32_t)ncols * 4u);
+            }
+            float2 x[RT][E2];
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const bool valid = r0 + r < re;
+                const float *xr = X + (r0 + r) * ldx + c0;
+#pragma unroll
+                for (int i = 0; i < NG; ++i) {
+                    const int col = (t + G * i) * 4;
+                    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (i < act && valid && col < ncols)
+                        q = __ldcs(reinterpret_cast<const float4 *>(xr + col));
+                    x[r][2 * i] = make_float2(q.x, q.y);
+                    x[r][2 * i + 1] = make_float2(q.z, q.w);
+                }
+            }
+            if (MODE != HH_MODE_W && tk.sign) cscale(x, tk.sign + c0, t, act, ncols);
+            // W: k = h..1; W^T: k = 1..h; S: k = 1..h, scale by d, k = h..1
+            for (int half = 0; half < (MODE == HH_MODE_SYM ? 2 : 1); ++half) {
+                if (half == 1) cscale(x, tk.d + c0, t, act, ncols);
+                const bool asc = MODE != HH_MODE_W && half == 0;
+                split::chain<G, NG, RT, RG, B, CL, true>(x, asc, h, vs, tk.tau, tk.gram, t, lane,
+                                                         warp, &rslot[rg][0], &rbar[rg][0], xc,
+                                                         err, act);
+            }
+            if (MODE != HH_MODE_WT && tk.sign) cscale(x, tk.sign + c0, t, act, ncols);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                if (r0 + r >= re) continue;
+                float *yr = Y + (r0 + r) * ldy + c0;
+#pragma unroll
+                for (int i = 0; i < NG; ++i) {
+                    if (i >= act) break;
+                    const int col = (t + G * i) * 4;
+                    if (col < ncols)
+                        __stcs(reinterpret_cast<float4 *>(yr + col),
+                               make_float4(x[r][2 * i].x, x[r][2 * i].y, x[r][2 * i + 1].x,
+                                           x[r][2 * i + 1].y));
+                }
+            }
+        }
+    }
+    // a reflector copy that was never seen complete gets one more bounded wait
+    if (tid == 0 && issued > confirmed) split::wait_cluster_bounded(&vbar, last_par);
+    // no CTA leaves while a peer may still store into its receive slots
+    __syncthreads();
+    split::cluster_sync();
+}
+
 // Fill p[0..count) with values in [-1, 1) from an integer hash of the index
 // (synthetic data for the autotuner's timing runs).
 __global__ void fill_kernel(float *p, int64_t count, uint32_t seed) {
@@ -294,6 +505,63 @@ static cudaError_t resident_per_sm(int dev, int *per_sm) {
     return cudaSuccess;
 }
 
+// ---- resident shape: co-resident clusters per device and cluster size ----
+static std::map<std::pair<int, int>, int> g_cluster_slots;
+
+template <int CL>
+static cudaError_t cluster_slots_cl(int *ncl) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(cluster_batch_kernel<HH_MODE_W, CL>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmem)) ||
+        (e = cudaFuncSetAttribute(cluster_batch_kernel<HH_MODE_WT, CL>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmem)) ||
+        (e = cudaFuncSetAttribute(cluster_batch_kernel<HH_MODE_SYM, CL>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmem)))
+        return e;
+    cudaLaunchConfig_t q = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    q.blockDim = dim3(kThreads);
+    q.gridDim = dim3(CL);
+    q.dynamicSmemBytes = kClusterSmem;
+    q.attrs = attr;
+    q.numAttrs = 1;
+    int nc = 0;
+    e = cudaOccupancyMaxActiveClusters(&nc, cluster_batch_kernel<HH_MODE_SYM, CL>, &q);
+    *ncl = nc > 0 ? nc : 1;
+    return e;
+}
+
+static cudaError_t cluster_slots(int dev, int cl, int *ncl) {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_cluster_slots.find({dev, cl});
+    if (it != g_cluster_slots.end()) {
+        *ncl = it->second;
+        return cudaSuccess;
+    }
+    cudaError_t e;
+    switch (cl) {
+        case 1: e = cluster_slots_cl<1>(ncl); break;
+        case 2: e = cluster_slots_cl<2>(ncl); break;
+        case 3: e = cluster_slots_cl<3>(ncl); break;
+        default: e = cluster_slots_cl<4>(ncl); break;
+    }
+    if (e == cudaSuccess) g_cluster_slots[{dev, cl}] = *ncl;
+    return e;
+}
+
+// Relative time of one row on the resident shape: per round of kCB
+// reflectors, FMAs over the widest CTA's granules plus the reduction (and the
+// exchange between CTAs), and the row's load and store.
+static double cluster_row_cost(int n, int h) {
+    const int cl = (n + kClusterHalf - 1) / kClusterHalf;
+    const int a = cl > 1 ? kCNG : (n + kCG * 4 - 1) / (kCG * 4);
+    return (double)((h + kCB - 1) / kCB) * (16.0 * a + (cl > 1 ? 12.0 : 4.0)) + 6.0 * a;
+}
+
 // ---- autotuner table: (n, h) -> shape ----
 struct TuneEntry {
     int shape = -1;
@@ -302,7 +570,9 @@ struct TuneEntry {
 static std::mutex g_tune_mu;
 static std::map<std::pair<int64_t, int64_t>, TuneEntry> g_tune;
 
-static bool shape_fits(int s, int64_t n) { return s >= 0 && s < kNumShapes && n <= shape_cover(s); }
+static bool shape_fits(int s, int64_t n, int64_t h) {
+    return s >= 0 && s < kNumShapes && n <= shape_cover(s) && (s != kClusterShape || h <= kClusterMaxH);
+}
 
 // Fixed rule: the smallest cover of n with 128 floats of state per thread
 // (64 for n <= 128), two reflectors per round.
@@ -318,12 +588,12 @@ static int default_shape(int64_t n) {
 static int lookup_shape(int64_t n, int64_t h) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find({n, h});
-    if (it != g_tune.end() && shape_fits(it->second.shape, n)) return it->second.shape;
+    if (it != g_tune.end() && shape_fits(it->second.shape, n, h)) return it->second.shape;
     // nearest tuned h for the same n (log distance; ties to the smaller h)
     int best = -1;
     double bd = 1e300;
     for (auto &kv : g_tune) {
-        if (kv.first.first != n || !shape_fits(kv.second.shape, n)) continue;
+        if (kv.first.first != n || !shape_fits(kv.second.shape, n, h)) continue;
         const double dist = fabs(log((double)(kv.first.second + 1) / (double)(h + 1)));
         if (dist < bd) {
             bd = dist;
@@ -334,6 +604,13 @@ static int lookup_shape(int64_t n, int64_t h) {
 }
 
 }  // namespace batched
+
+// One launch of the resident shape: its tasks have (CL-1)*512 < n <= CL*512.
+struct CPart {
+    int grid = 0, nitems = 0, hmax = 0;  // clusters launched, items, largest h
+    batched::CItem *d_items = nullptr;   // items, grouped by cluster in cluster order
+    int *d_cstart = nullptr;             // cluster c: items cstart[c] .. cstart[c+1]-1
+};
 
 // A batch: the device work list, the task table and one graph per mode.
 struct Batch {
@@ -347,7 +624,13 @@ struct Batch {
     batched::Task *d_tasks = nullptr;
     batched::Item *d_items = nullptr;
     int *d_counter = nullptr, *d_err = nullptr;
+    CPart cpart[batched::kClusterMaxCL];  // resident-shape launches, CL = 1..4
     cudaStream_t capture = nullptr;
+#if HH_BATCH_FORK
+    // launches of one graph on parallel branches (fork, then one join per launch)
+    cudaStream_t side[batched::kClusterMaxCL + 1] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[batched::kClusterMaxCL + 1] = {};
+#endif
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
     // the last launch (its stream and completion event): a launch on another
@@ -364,6 +647,17 @@ static void free_batch(Batch *b) {
         if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
     }
     if (b->capture) cudaStreamDestroy(b->capture);
+#if HH_BATCH_FORK
+    for (int j = 0; j <= batched::kClusterMaxCL; ++j) {
+        if (b->side[j]) cudaStreamDestroy(b->side[j]);
+        if (b->join_ev[j]) cudaEventDestroy(b->join_ev[j]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+#endif
+    for (auto &cp : b->cpart) {
+        cudaFree(cp.d_items);
+        cudaFree(cp.d_cstart);
+    }
     if (b->upload_done) cudaEventDestroy(b->upload_done);
     if (b->done) cudaEventDestroy(b->done);
     cudaFreeHost(b->pinned);
@@ -418,10 +712,10 @@ static hh_status batch_create(Batch **out, int count, const hh_plan_t *plans, co
         }
         int s = force_shape ? force_shape[i] : -1;
         if (s < 0) s = lookup_shape(p->n, p->h);
-        if (!shape_fits(s, p->n)) {
+        if (!shape_fits(s, p->n, p->h)) {
             free_batch(b);
-            return fail(HH_ERR_INVALID_ARG, "plan %d: shape %d does not cover n = %lld", i, s,
-                        (long long)p->n);
+            return fail(HH_ERR_INVALID_ARG, "plan %d: shape %d does not cover n = %lld, h = %lld",
+                        i, s, (long long)p->n, (long long)p->h);
         }
         b->plans[i] = p;
         b->shapes[i] = s;
@@ -441,7 +735,7 @@ static hh_status batch_create(Batch **out, int count, const hh_plan_t *plans, co
         t.rows_per_tile = shape_rows(s);
         tile_cost[i] = (double)shape_rows(s) * (4.0 * p->n * (double)p->h + 96.0 * p->n);
         const int64_t tiles = (rows[i] + t.rows_per_tile - 1) / t.rows_per_tile;
-        total += tile_cost[i] * (double)tiles;
+        if (s != kClusterShape) total += tile_cost[i] * (double)tiles;
     }
     int per_sm = 1, sms = 1;
     if ((e = resident_per_sm(dev, &per_sm)) ||
@@ -456,6 +750,7 @@ static hh_status batch_create(Batch **out, int count, const hh_plan_t *plans, co
     std::vector<double> icost;
     for (int i = 0; i < count; ++i) {
         const Task &t = b->tasks[i];
+        if (t.shape == kClusterShape) continue;  // scheduled below
         const int64_t tiles = (t.rows + t.rows_per_tile - 1) / t.rows_per_tile;
         int64_t per = (int64_t)(target / tile_cost[i]);
         if (per < 1) per = 1;
@@ -492,8 +787,149 @@ static hh_status batch_create(Batch **out, int count, const hh_plan_t *plans, co
         free_batch(b);
         return cuda_fail(e, "batch allocation");
     }
+#if HH_BATCH_FORK
+    if ((e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming))) {
+        free_batch(b);
+        return cuda_fail(e, "batch allocation");
+    }
+    for (int j = 0; j <= kClusterMaxCL; ++j)
+        if ((e = cudaStreamCreateWithFlags(&b->side[j], cudaStreamNonBlocking)) ||
+            (e = cudaEventCreateWithFlags(&b->join_ev[j], cudaEventDisableTiming))) {
+            free_batch(b);
+            return cuda_fail(e, "batch allocation");
+        }
+#endif
+    // Resident-shape tasks: one launch per cluster size CL, each with a static
+    // schedule.  The tasks' rows, in task order, are cut into runs of
+    // kClusterUnit rows; a run goes to the cluster whose share of the launch's
+    // total cost (cluster_row_cost per row) holds the run's midpoint, so each
+    // cluster gets a contiguous stretch of the task list and loads each of its
+    // tasks' reflectors once.
+    for (int cl = 1; cl <= kClusterMaxCL; ++cl) {
+        std::vector<int> ids;
+        double wsum = 0;
+        int64_t units = 0;
+        int hmax = 0;
+        for (int i = 0; i < count; ++i) {
+            const Task &t = b->tasks[i];
+            if (t.shape != kClusterShape || t.rows == 0) continue;
+            if ((t.n + kClusterHalf - 1) / kClusterHalf != cl) continue;
+            ids.push_back(i);
+            wsum += cluster_row_cost(t.n, t.h) * (double)t.rows;
+            units += (t.rows + kClusterUnit - 1) / kClusterUnit;
+            hmax = std::max(hmax, t.h);
+        }
+        if (ids.empty()) continue;
+        int ncl = 1;
+        if ((e = cluster_slots(dev, cl, &ncl))) {
+            free_batch(b);
+            return cuda_fail(e, "resident-shape attributes");
+        }
+        const int grid = (int)std::min<int64_t>(ncl, units);
+        const double share = wsum / grid;
+        std::vector<CItem> its;
+        std::vector<int> owner;
+        double cum = 0;
+        for (int i : ids) {
+            const Task &t = b->tasks[i];
+            const double uc = cluster_row_cost(t.n, t.h);
+            for (int64_t r = 0; r < t.rows; r += kClusterUnit) {
+                const int64_t r1 = std::min<int64_t>(t.rows, r + kClusterUnit);
+                const double mid = cum + 0.5 * uc * (double)(r1 - r);
+                const int k = std::min(grid - 1, (int)(mid / share));
+                if (!its.empty() && its.back().task == i && owner.back() == k)
+                    its.back().r1 = r1;
+                else {
+                    its.push_back(CItem{i, 0, r, r1});
+                    owner.push_back(k);
+                }
+                cum += uc * (double)(r1 - r);
+            }
+        }
+        // owner is non-decreasing: the items are already grouped by cluster
+        std::vector<int> cstart(grid + 1, 0);
+        for (int k : owner) ++cstart[k + 1];
+        for (int k = 0; k < grid; ++k) cstart[k + 1] += cstart[k];
+        CPart &cp = b->cpart[cl - 1];
+        cp.grid = grid;
+        cp.nitems = (int)its.size();
+        cp.hmax = hmax;
+        if ((e = dev_malloc(&cp.d_items, sizeof(CItem) * its.size())) ||
+            (e = dev_malloc(&cp.d_cstart, sizeof(int) * cstart.size())) ||
+            (e = cudaMemcpy(cp.d_items, its.data(), sizeof(CItem) * its.size(),
+                            cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(cp.d_cstart, cstart.data(), sizeof(int) * cstart.size(),
+                            cudaMemcpyHostToDevice))) {
+            free_batch(b);
+            return cuda_fail(e, "batch allocation");
+        }
+    }
     *out = b;
     return HH_OK;
+}
+
+// Items of every launch of the batch.
+static int64_t batch_items(const Batch *b) {
+    int64_t n = b->nitems;
+    for (const CPart &cp : b->cpart) n += cp.nitems;
+    return n;
+}
+
+// One resident-shape launch of CL-CTA clusters on stream s.
+template <int CL>
+static cudaError_t launch_cluster(const Batch *b, const CPart &cp, int mode, cudaStream_t s) {
+    using namespace batched;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.gridDim = dim3(CL * cp.grid);
+    cfg.dynamicSmemBytes = cp.hmax > 0 ? (size_t)cp.hmax * kClusterHalf * 4 : 16;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const Task *tasks = b->d_tasks;
+    const CItem *items = cp.d_items;
+    const int *cstart = cp.d_cstart;
+    switch (mode) {
+        case HH_MODE_W:
+            return cudaLaunchKernelEx(&cfg, cluster_batch_kernel<HH_MODE_W, CL>, tasks, items,
+                                      cstart, b->d_err);
+        case HH_MODE_WT:
+            return cudaLaunchKernelEx(&cfg, cluster_batch_kernel<HH_MODE_WT, CL>, tasks, items,
+                                      cstart, b->d_err);
+        default:
+            return cudaLaunchKernelEx(&cfg, cluster_batch_kernel<HH_MODE_SYM, CL>, tasks, items,
+                                      cstart, b->d_err);
+    }
+}
+
+// Launch j of the batch (0..kClusterMaxCL-1: the resident shape with
+// CL = kClusterMaxCL - j; kClusterMaxCL: the staged shapes) on stream s, if
+// it has work.
+static cudaError_t launch_part(const Batch *b, int j, int mode, cudaStream_t s) {
+    using namespace batched;
+    if (j == kClusterMaxCL) {
+        if (b->nitems == 0) return cudaSuccess;
+        cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        batched_chain_kernel<<<b->grid, kThreads, kStageBytes, s>>>(b->d_tasks, b->d_items,
+                                                                    b->nitems, b->d_counter, mode,
+                                                                    b->d_err);
+        return cudaGetLastError();
+    }
+    const int cl = kClusterMaxCL - j;
+    const CPart &cp = b->cpart[cl - 1];
+    if (cp.nitems == 0) return cudaSuccess;
+    switch (cl) {
+        case 1: return launch_cluster<1>(b, cp, mode, s);
+        case 2: return launch_cluster<2>(b, cp, mode, s);
+        case 3: return launch_cluster<3>(b, cp, mode, s);
+        default: return launch_cluster<4>(b, cp, mode, s);
+    }
 }
 
 static hh_status batch_graph(Batch *b, int mode) {
@@ -501,10 +937,24 @@ static hh_status batch_graph(Batch *b, int mode) {
     cudaError_t e;
     if ((e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal)))
         return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->capture);
-    batched::batched_chain_kernel<<<b->grid, batched::kThreads, batched::kStageBytes, b->capture>>>(
-        b->d_tasks, b->d_items, b->nitems, b->d_counter, mode, b->d_err);
-    cudaError_t le = cudaGetLastError();
+    // the launches in order: resident shape with four, three, two and one CTAs
+    // per cluster, then the staged shapes
+    cudaError_t le = cudaSuccess;
+#if HH_BATCH_FORK
+    // on parallel branches of the graph, so that one launch's last CTAs share
+    // the GPU with the next launch's first
+    le = cudaEventRecord(b->fork_ev, b->capture);
+    for (int j = 0; j <= batched::kClusterMaxCL && le == cudaSuccess; ++j) {
+        if ((le = cudaStreamWaitEvent(b->side[j], b->fork_ev, 0)) ||
+            (le = launch_part(b, j, mode, b->side[j])) ||
+            (le = cudaEventRecord(b->join_ev[j], b->side[j])))
+            break;
+        le = cudaStreamWaitEvent(b->capture, b->join_ev[j], 0);
+    }
+#else
+    for (int j = 0; j <= batched::kClusterMaxCL && le == cudaSuccess; ++j)
+        le = launch_part(b, j, mode, b->capture);
+#endif
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->capture, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
@@ -561,7 +1011,7 @@ static hh_status batch_apply(Batch *b, int mode, const void *const *X, const int
         t.ldx = lx;
         t.ldy = ly;
     }
-    if (b->nitems == 0) return HH_OK;  // nothing to launch
+    if (batch_items(b) == 0) return HH_OK;  // nothing to launch
     hh_status st = batch_graph(b, mode);
     if (st) return st;
     // the previous launch on another stream still owns the counter and the table
@@ -626,8 +1076,14 @@ hh_status hh_batch_sync(hh_batch_t batch, void *stream) {
 hh_status hh_batch_info(hh_batch_t batch, int64_t *nitems, int *grid, int *shapes) {
     const Batch *b = reinterpret_cast<const Batch *>(batch);
     if (!b) return fail(HH_ERR_INVALID_ARG, "batch is NULL");
-    if (nitems) *nitems = b->nitems;
-    if (grid) *grid = b->grid;
+    if (nitems) *nitems = batch_items(b);
+    if (grid) {
+        // CTAs of the largest launch
+        int g = b->grid;
+        for (int cl = 1; cl <= batched::kClusterMaxCL; ++cl)
+            g = std::max(g, cl * b->cpart[cl - 1].grid);
+        *grid = g;
+    }
     if (shapes)
         for (int i = 0; i < b->count; ++i) shapes[i] = b->shapes[i];
     return HH_OK;
@@ -660,11 +1116,22 @@ hh_status hh_batch_shape(int shape, int *G, int *NG, int *RT, int *rows_per_tile
 
 int hh_batch_num_shapes(void) { return batched::kNumShapes; }
 
+hh_status hh_batch_shape_limits(int shape, int *max_h, int *max_cluster) {
+    using namespace batched;
+    if (shape < 0 || shape >= kNumShapes)
+        return fail(HH_ERR_INVALID_ARG, "shape %d outside [0, %d)", shape, kNumShapes);
+    const bool res = shape == kClusterShape;
+    if (max_h) *max_h = res ? kClusterMaxH : -1;
+    if (max_cluster) *max_cluster = res ? kClusterMaxCL : 0;
+    return HH_OK;
+}
+
 hh_status hh_tune_set(int64_t n, int64_t h, int shape) {
     using namespace batched;
     if (n < 1 || h < 0) return fail(HH_ERR_INVALID_ARG, "n = %lld, h = %lld", (long long)n, (long long)h);
-    if (!shape_fits(shape, n))
-        return fail(HH_ERR_INVALID_ARG, "shape %d does not cover n = %lld", shape, (long long)n);
+    if (!shape_fits(shape, n, h))
+        return fail(HH_ERR_INVALID_ARG, "shape %d does not cover n = %lld, h = %lld", shape,
+                    (long long)n, (long long)h);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneEntry &t = g_tune[{n, h}];
     t.shape = shape;
@@ -721,7 +1188,7 @@ hh_status hh_tune_load(const char *path) {
         int s = -1;
         char extra = 0;
         if (sscanf(c, "%lld %lld %d %c", &n, &h, &s, &extra) != 3 || n < 1 || h < 0 ||
-            !batched::shape_fits(s, n)) {
+            !batched::shape_fits(s, n, h)) {
             fclose(f);
             return fail(HH_ERR_INVALID_ARG, "%s:%d: expected 'n h shape' with a shape covering n",
                         path, lineno);
@@ -778,7 +1245,7 @@ hh_status hh_tune(const int64_t *ns, int nn, const int64_t *hs, int nh, int64_t 
             float best = INFINITY;
             for (int sh = 0; sh < kNumShapes && !st; ++sh) {
                 ent.ms[sh] = NAN;
-                if (!shape_fits(sh, n)) continue;
+                if (!shape_fits(sh, n, h)) continue;
                 Batch *b = nullptr;
                 st = batch_create(&b, 1, &plan, &rows, &sh);
                 if (st) break;

@@ -168,15 +168,19 @@ struct Exchange {
 
 // Apply h reflectors, ascending (k = 0..h-1) or descending, to the RT rows in
 // x, B per round.  vs holds this CTA's half of every reflector (row k at
-// vs + k*HALF).
-template <int G, int NG, int RT, int RG, int B, int CL>
+// vs + k*HALF).  With PART, granule indices i >= act (warp-uniform: their
+// columns lie past this CTA's share of n) are neither read nor computed; the
+// remaining terms are summed in the same order.
+template <int G, int NG, int RT, int RG, int B, int CL, bool PART = false>
 __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2], bool asc, int h,
                                       const float *vs, const float *__restrict__ tau,
                                       const float *__restrict__ gram, int t, int lane, int warp,
-                                      float *slot, uint64_t *bars, Exchange<CL> &xc, int *err) {
+                                      float *slot, uint64_t *bars, Exchange<CL> &xc, int *err,
+                                      int act = NG) {
     using C = XCfg<G, NG, RT, RG, B>;
     constexpr int E2 = C::E2, NW = C::NW, NV = C::NV, L = C::L, HALF = C::HALF;
     (void)NW;
+    (void)act;
     auto load_u = [&](int s0, int j, float2(&dst)[E2]) {
         const bool ok = s0 + j < h;
         const int k = asc ? s0 + j : h - 1 - s0 - j;
@@ -184,7 +188,7 @@ __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2
 #pragma unroll
         for (int i = 0; i < NG; ++i) {
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ok) q = row[t + G * i];
+            if (ok && (!PART || i < act)) q = row[t + G * i];
             dst[2 * i] = make_float2(q.x, q.y);
             dst[2 * i + 1] = make_float2(q.z, q.w);
         }
@@ -214,8 +218,17 @@ __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
                 float2 a = make_float2(0.f, 0.f);
+                if constexpr (PART) {
 #pragma unroll
-                for (int e = 0; e < E2; ++e) a = __ffma2_rn(x[r][e], u[e], a);
+                    for (int i = 0; i < NG; ++i) {
+                        if (i >= act) continue;
+                        a = __ffma2_rn(x[r][2 * i], u[2 * i], a);
+                        a = __ffma2_rn(x[r][2 * i + 1], u[2 * i + 1], a);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E2; ++e) a = __ffma2_rn(x[r][e], u[e], a);
+                }
                 p[j * RT + r] = a.x + a.y;
             }
         }
@@ -286,8 +299,17 @@ __device__ __forceinline__ void chain(float2 (&x)[RT][XCfg<G, NG, RT, RG, B>::E2
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
                 const float2 cc = make_float2(c[j][r], c[j][r]);
+                if constexpr (PART) {
 #pragma unroll
-                for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(u[e], cc, x[r][e]);
+                    for (int i = 0; i < NG; ++i) {
+                        if (i >= act) continue;
+                        x[r][2 * i] = __ffma2_rn(u[2 * i], cc, x[r][2 * i]);
+                        x[r][2 * i + 1] = __ffma2_rn(u[2 * i + 1], cc, x[r][2 * i + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E2; ++e) x[r][e] = __ffma2_rn(u[e], cc, x[r][e]);
+                }
             }
         }
     }

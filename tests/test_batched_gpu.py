@@ -103,12 +103,12 @@ def test_batched_ragged_matches_oracle(mode):
     batch.close()
 
 
-@pytest.mark.parametrize("shape", range(10))
+@pytest.mark.parametrize("shape", range(11))
 def test_every_tile_shape(shape):
     """Each compiled shape, at its full cover, one granule short, and ragged."""
     hh = _hh()
     shapes = hh.batch_shapes()
-    assert len(shapes) == 10
+    assert len(shapes) == 11
     cover = shapes[shape]["cover"]
     ns = sorted({cover, max(4, cover - 64), max(4, cover // 2 + 4), max(4, cover - 124)})
     specs = [(n, h, b, 100 + 10 * shape + j)
@@ -127,6 +127,83 @@ def test_every_tile_shape(shape):
             batch.sync()
             _check(data, Xs, Ys, mode)
         batch.close()
+    finally:
+        hh.tune_clear()
+
+
+def _resident_shape():
+    shapes = _hh().batch_shapes()
+    return next(k for k, s in enumerate(shapes) if s["max_cluster"] > 0)
+
+
+RESIDENT = [
+    # (n, h, batch, seed): clusters of one to four CTAs (512 columns each), n
+    # ragged inside a CTA's columns, h = 0, 1 and the largest, empty and
+    # one-row batches, batches that are not a multiple of the 64-row unit
+    (4, 3, 70, 31), (68, 16, 129, 32), (128, 1, 64, 33), (500, 100, 65, 34),
+    (512, 0, 40, 35), (516, 9, 300, 36), (700, 33, 1, 37), (1024, 64, 257, 38),
+    (1028, 5, 128, 39), (1300, 17, 0, 40), (1536, 100, 63, 41), (1540, 2, 191, 42),
+    (1996, 40, 77, 43), (2048, 64, 130, 44),
+]
+
+
+@pytest.mark.parametrize("mode", ["W", "WT", "SYM"])
+@pytest.mark.parametrize("ld_extra", [0, 12])
+def test_resident_shape_matches_oracle(mode, ld_extra):
+    """The resident-reflector shape on every cluster size, against the oracle;
+    strided rows padded with NaN (nothing past n is read), then in place."""
+    hh = _hh()
+    r = _resident_shape()
+    hh.tune_clear()
+    for n, h, _, _ in RESIDENT:
+        hh.tune_set(n, h, r)
+    try:
+        plans, data = _make(RESIDENT)
+        with hh.Batch(plans, [x.shape[0] for (_, _, _, x) in data]) as batch:
+            assert batch.info()["shapes"] == [r] * len(RESIDENT)
+            Xs = _inputs(data, ld_extra)
+            Ys = [torch.full_like(X, float("nan")) for X in Xs]
+            batch.apply(Xs, Ys, mode=mode)
+            batch.sync()
+            _check(data, Xs, Ys, mode)
+            X0 = [X.clone() for X in Xs]
+            batch.apply(Xs, Xs, mode=mode)  # in place
+            batch.sync()
+            _check(data, X0, Xs, mode)
+    finally:
+        hh.tune_clear()
+
+
+def test_resident_shape_many_transforms_per_cluster():
+    """Far more transforms than clusters of each size, so that a cluster walks
+    several tasks and reloads reflectors between them; mixed with staged-shape
+    transforms in the same batch (both kinds of launch in one graph), replayed."""
+    hh = _hh()
+    r = _resident_shape()
+    rng = np.random.default_rng(5)
+    specs = []
+    for j in range(160):
+        n = int(rng.integers(1, 33)) * 64
+        h = int(rng.integers(0, 25))
+        specs.append((n, h, int(rng.integers(0, 400)), 500 + j))
+    hh.tune_clear()
+    for j, (n, h, _, _) in enumerate(specs):
+        hh.tune_set(n, h, r if j % 5 else 3 if n <= 1024 else 6)
+    try:
+        plans, data = _make(specs)
+        with hh.Batch(plans, [x.shape[0] for (_, _, _, x) in data]) as batch:
+            got = batch.info()["shapes"]
+            assert got.count(r) > 100 and got.count(r) < len(specs)
+            Xs = _inputs(data)
+            for mode in ("W", "SYM"):
+                Ys = [torch.full_like(X, float("nan")) for X in Xs]
+                batch.apply(Xs, Ys, mode=mode)
+                batch.sync()
+                _check(data, Xs, Ys, mode)
+                Y2 = [torch.full_like(X, float("nan")) for X in Xs]
+                batch.apply(Xs, Y2, mode=mode)  # the captured graph, replayed on new buffers
+                batch.sync()
+                assert all(torch.equal(a, b) for a, b in zip(Ys, Y2))
     finally:
         hh.tune_clear()
 

@@ -61,10 +61,18 @@ def test_batch_shapes_and_tune_table_without_device(L, tmp_path):
     shapes = hh.batch_shapes()
     assert len(shapes) == L.hh_batch_num_shapes() >= 2
     for s in shapes:
-        assert s["cover"] == s["G"] * s["NG"] * 4
-        # every shape stages ROWS x COVER floats in at most 128 KB of shared
-        # memory: 256 threads holding 64 or 128 floats of vector state each
-        assert s["rows_per_tile"] * s["cover"] * 4 in (65536, 131072)
+        if s["max_cluster"] == 0:
+            assert s["cover"] == s["G"] * s["NG"] * 4 and s["max_h"] == -1
+            # every staged shape stages ROWS x COVER floats in at most 128 KB of
+            # shared memory: 256 threads holding 64 or 128 floats of vector state each
+            assert s["rows_per_tile"] * s["cover"] * 4 in (65536, 131072)
+        else:
+            # the resident shape: G * NG * 4 columns per CTA, up to max_cluster CTAs,
+            # and its CTA's columns of max_h reflectors in 200 KiB of shared memory
+            assert s["cover"] == s["G"] * s["NG"] * 4 * s["max_cluster"]
+            assert s["max_h"] * s["G"] * s["NG"] * 4 * 4 <= 200 * 1024
+    resident = [k for k, s in enumerate(shapes) if s["max_cluster"] > 0]
+    assert len(resident) == 1
     covers = sorted({s["cover"] for s in shapes})
     assert covers[-1] >= 4096
     hh.tune_clear()
@@ -95,6 +103,20 @@ def test_batch_shapes_and_tune_table_without_device(L, tmp_path):
     bad.write_text("4096 8 %d\n" % small)
     with pytest.raises(hh.HHError, match="INVALID_ARG"):
         hh.tune_load(str(bad))
+    # the resident shape takes h <= max_h and n <= its cover
+    r = resident[0]
+    hh.tune_set(shapes[r]["cover"], shapes[r]["max_h"], r)
+    assert hh.tune_get(shapes[r]["cover"], shapes[r]["max_h"])[0] == r
+    for n, h in ((shapes[r]["cover"], shapes[r]["max_h"] + 1), (shapes[r]["cover"] + 4, 8)):
+        with pytest.raises(hh.HHError, match="INVALID_ARG"):
+            hh.tune_set(n, h, r)
+    # a tuned resident entry is not taken for an h above its limit
+    hh.tune_set(600, 8, r)
+    assert hh.tune_get(600, 8)[0] == r
+    assert hh.tune_get(600, shapes[r]["max_h"] + 50)[0] != r
+    bad.write_text("600 %d %d\n" % (shapes[r]["max_h"] + 1, r))
+    with pytest.raises(hh.HHError, match="INVALID_ARG"):
+        hh.tune_load(str(bad))
     bad.write_text("128 x 0\n")
     with pytest.raises(hh.HHError, match="INVALID_ARG"):
         hh.tune_load(str(bad))
@@ -114,6 +136,8 @@ def test_batch_errors_without_device(L):
     st = L.hh_batch_apply(None, 0, None, None, None, None, None)
     assert _lib.STATUS[st] == "HH_ERR_INVALID_ARG"
     assert _lib.STATUS[L.hh_batch_shape(-1, None, None, None, None, None)] == "HH_ERR_INVALID_ARG"
+    n = L.hh_batch_num_shapes()
+    assert _lib.STATUS[L.hh_batch_shape_limits(n, None, None)] == "HH_ERR_INVALID_ARG"
     st = L.hh_tune(None, 1, None, 1, 16, None)
     assert _lib.STATUS[st] == "HH_ERR_INVALID_ARG"
 
