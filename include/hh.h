@@ -306,8 +306,8 @@ hh_status hh_batch_apply(hh_batch_t batch, hh_mode mode, const void *const *X, c
  * `stream`. */
 hh_status hh_batch_sync(hh_batch_t batch, void *stream);
 
-/* Work-list size, grid size, and the tile shape of each transform (count ints,
- * or NULL). */
+/* Work items of all the batch's launches, CTAs of its largest launch, and the
+ * tile shape of each transform (count ints, or NULL). */
 hh_status hh_batch_info(hh_batch_t batch, int64_t *nitems, int *grid, int *shapes);
 
 /* Synchronises the device, then frees the batch.  NULL is a no-op. */

@@ -176,11 +176,18 @@ def test_mahalanobis_full_size():
     plan.close()
 
 
-def test_batched_512_transforms_full_size():
+@pytest.mark.parametrize("shapes", ["fixed", "resident"])
+def test_batched_512_transforms_full_size(shapes):
+    """The 512 ragged transforms at full batch: on the fixed staged-shape rule, and with every
+    transform on the resident-reflector shape (all four cluster sizes, parallel graph branches)."""
     import paper_1811_07624_gb300 as hh
 
     specs = [(t["n"], t["h"], t["batch"], t["seed"]) for t in si.ragged_transforms(512)]
     hh.tune_clear()  # the fixed shape rule; the tuned shapes are covered by the batched tests
+    if shapes == "resident":
+        r = next(k for k, s in enumerate(hh.batch_shapes()) if s["max_cluster"] > 0)
+        for n, h, _, _ in specs:
+            hh.tune_set(n, h, r)
     Us = [torch.tensor(si.reflectors(n, h, seed=sd), dtype=torch.float32) for n, h, _, sd in specs]
     plans = [hh.Plan(U.to(DEV)) for U in Us]
     total = sum(n * b for n, _, b, _ in specs)
@@ -193,6 +200,8 @@ def test_batched_512_transforms_full_size():
         Ys.append(Ybuf[off:off + n * b].view(b, n))
         off += n * b
     with hh.Batch(plans, [b for _, _, b, _ in specs]) as batch:
+        if shapes == "resident":
+            assert batch.info()["shapes"] == [r] * len(specs)
         batch.apply(Xs, Ys, mode="W")
         batch.sync()
     assert bool(torch.isfinite(Ybuf).all()), "an output was not written"
@@ -204,6 +213,7 @@ def test_batched_512_transforms_full_size():
     assert worst <= 1e-5, f"worst transform: {worst:.2e}"
     for p in plans:
         p.close()
+    hh.tune_clear()
 
 
 def test_mahalanobis_grad_full_size():
