@@ -262,12 +262,15 @@ class Plan:
 
 # -- batched persistent launch ------------------------------------------------------
 class Batch:
-    """Many transforms applied in one persistent, graph-replayed launch.
+    """Many transforms applied in one graph-replayed launch (hh_batch_*).
 
     plans: F32 plans (n % 4 == 0, n <= 4096); batches: rows per plan.  The
     tile shape of each transform comes from the autotuner's table at creation
-    (:func:`tune`, :func:`tune_load`, :func:`tune_set`).  The batch keeps its
-    plans alive.
+    (:func:`tune`, :func:`tune_load`, :func:`tune_set`): a staged shape, run by
+    one persistent kernel on a shared work counter, or the resident-reflector
+    shape (n <= 2048, h <= 100), run by one kernel per cluster size on a static
+    schedule; all of them replay as one CUDA graph.  The batch keeps its plans
+    alive.
     """
 
     def __init__(self, plans, batches):
